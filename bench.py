@@ -1,0 +1,302 @@
+"""Benchmark: RR sets/s of full D-SSA solves on a resident synthetic R-MAT graph.
+
+One step = one complete D-SSA solve (Algorithm 4) on the GPU: RR sampling of
+every doubling round, node->set index, greedy Max-Coverage, the stare check
+and the host FP64 stopping rule.  Workload: directed R-MAT, 2^20 nodes, 2^24
+draws (a,b,c,d = 0.57,0.19,0.19,0.05; duplicates and self-loops removed), IC
+with trivalency weights, k=100, eps=0.1, delta=1/n; each step uses a fresh
+Philox seed.  value = RR sets generated / device time; e2e repeats the steps
+through the C ABI from pinned host edge arrays (graph upload and CSR build
+inside the timed region).
+
+--impl reference times the plain CPU oracle on a bounded sample of the same
+workload (the RR sets of the first samples of the solve's stream).
+Multi-GPU (torchrun): independent replicas, one per rank, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (scale, m_draw, weighting, algo, model, k, eps)
+    "dssa_ic_trivalency_rmat20_m16M_k100": (20, 1 << 24, 1, 1, 0, 100, 0.1),
+    "ssa_ic_wc_rmat14_m128K_k50": (14, 1 << 17, 0, 0, 0, 50, 0.1),
+    "dssa_lt_wc_rmat23_m128M_k500": (23, 1 << 27, 0, 1, 1, 500, 0.05),
+}
+DEFAULT = "dssa_ic_trivalency_rmat20_m16M_k100"
+METRIC, UNIT = "RR sets/s", "RR sets/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) run during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id, self.proc, self.lines = gpu_id, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_graph_inputs(name):
+    import inputs
+    scale, m_draw, weighting, algo, model, k, eps = WORKLOADS[name]
+    el = inputs.rmat(scale, m_draw, 0.57, 0.19, 0.19, seed=1)
+    return el, weighting, algo, model, k, eps
+
+
+def cpu_baseline(el, weighting, model, seed, budget_s):
+    """The oracle as it stands, single-threaded: RR sets of the solve's stream for ~budget_s."""
+    import oracle
+    oracle.build()
+    og = oracle.Graph(el.n, el.src, el.dst, weighting, None, 1)
+    pool = oracle.Pool(og, model, seed, 0)
+    t0 = time.perf_counter()
+    count, chunk = 0, 4
+    while time.perf_counter() - t0 < budget_s:
+        count += chunk
+        pool.grow(count)
+        chunk = min(chunk * 2, 64)
+    dt = time.perf_counter() - t0
+    return count, dt, pool.edge_visits
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    name = args.workload
+    el, weighting, algo, model, k, eps = make_graph_inputs(name)
+    import oracle
+    oracle.build()
+    og = oracle.Graph(el.n, el.src, el.dst, weighting, None, 1)
+    per_step = args.ref_sets
+    times, counts = [], []
+    for s in range(args.warmup + args.steps):
+        pool = oracle.Pool(og, model, 1 + s, 0)
+        t0 = time.perf_counter()
+        pool.grow(per_step)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            counts.append(per_step)
+    total_t = sum(times)
+    value = sum(counts) / total_t
+    sample = (f"first {per_step} RR sets of the D-SSA stream (Philox seed = step index + 1) of the workload, "
+              f"sampling only, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": name, "n": el.n, "m": el.m, "k": k, "eps": eps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-sets", type=int, default=150)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1605_07990_gb300 as P
+
+    name = args.workload
+    el, weighting, algo, model, k, eps = make_graph_inputs(name)
+    delta = 1.0 / el.n
+    g = P.ssa_load_graph(el.n, el.src, el.dst, None, weighting, 1)
+    stream = torch.cuda.current_stream()
+    solver = P.Solver(g, stream=stream.cuda_stream)
+
+    def seed_of(step):
+        return 1 + step + 1000 * rank
+
+    for w in range(args.warmup):
+        solver.solve(algo, model, k, eps, delta, 10_000 + w + 1000 * rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    try:
+        gpu_id = torch.cuda.get_device_properties(local).uuid
+        gpu_id = f"GPU-{gpu_id}" if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    except Exception:
+        gpu_id = local
+    clk = Clocks(gpu_id)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    e0.record(stream)
+    for s in range(args.steps):
+        results.append(solver.solve(algo, model, k, eps, delta, seed_of(s), want_kstats=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    rr = sum(r.n_rr for r in results)
+    ev = sum(r.edge_visits for r in results)
+    nv = sum(r.node_visits for r in results)
+    launches = sum(r.kernel_launches for r in results)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        c = torch.tensor([rr, ev, nv], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        rr_all, ev_all, nv_all = (float(x) for x in c.tolist())
+    else:
+        ms_max, rr_all, ev_all, nv_all = ms, float(rr), float(ev), float(nv)
+    value = rr_all / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel class (CUDA events inside the library, same stream)
+    ks = {c: {"launches": sum(r.kstats[c]["launches"] for r in results),
+              "ms": sum(r.kstats[c]["ms"] for r in results)} for c in P.binding.KERNEL_CLASSES}
+    dom = max(ks, key=lambda c: ks[c]["ms"])
+    cta_ev = sum(r.cta_edge_visits for r in results)
+    cta_nv = sum(r.cta_node_visits for r in results)
+    cta_sets = sum(r.cta_sets for r in results)
+    # algorithmic bytes: 8 per examined in-edge ({src,thr}), 16 per visited node (two CSR offsets)
+    # + 8 per stored pool entry (node, sample id), 12 per stored set (start, length)
+    stored = sum(r.pool_entries for r in results)
+    if dom == "sample_cta":
+        abytes = 8 * cta_ev + 24 * cta_nv + 12 * cta_sets
+    elif dom == "sample_warp":
+        abytes = 8 * (ev - cta_ev) + 16 * (nv - cta_nv) + 8 * (stored - cta_nv) + 12 * sum(r.n_rr for r in results)
+    else:
+        abytes = None
+    peak, peak_kind = peaks()
+    roof = None
+    if abytes is not None and ks[dom]["ms"] > 0:
+        ach = abytes / (ks[dom]["ms"] / 1000.0) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": peak_kind, "traffic": None,
+                "bytes_per_launch": abytes / max(1, ks[dom]["launches"]),
+                "avg_launch_ms": ks[dom]["ms"] / max(1, ks[dom]["launches"])}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": name, "n": el.n, "m": el.m, "algo": "D-SSA" if algo else "SSA",
+                       "model": "LT" if model else "IC",
+                       "weights": ["weighted-cascade", "trivalency"][weighting], "k": k, "eps": eps,
+                       "delta": "1/n", "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (CSR 137 MB; RR pool several GB per solve)"},
+            "edge_visits_per_s": ev_all / (ms_max / 1000.0), "node_visits_per_s": nv_all / (ms_max / 1000.0),
+            "rr_sets_per_solve": rr / args.steps, "rounds": [r.rounds for r in results],
+            "kernel_ms": ks, "gpu_launches": launches, "clocks": clocks, "roofline": roof}
+
+    # end to end through the C ABI: pinned host edges -> graph upload/CSR build -> solve -> seeds to host
+    src_h = torch.from_numpy(el.src).pin_memory()
+    dst_h = torch.from_numpy(el.dst).pin_memory()
+    src_np, dst_np = src_h.numpy(), dst_h.numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rr_e2e = 0
+    for s in range(args.e2e_steps):
+        g2 = P.ssa_load_graph(el.n, src_np, dst_np, None, weighting, 1)
+        r = P.ssa_solve(g2, algo, model, k, eps, delta, 500 + seed_of(s))
+        rr_e2e += r.n_rr
+        g2.free()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    line["e2e"] = {"value": rr_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(el.m * 8),
+                   "d2h_bytes_per_step": int(k * 4 + 64), "steps": args.e2e_steps,
+                   "includes": "graph upload + device CSR build + solve + seeds to host"}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cnt, dt, cev = cpu_baseline(el, weighting, model, seed_of(0), args.cpu_seconds)
+        line["cpu_baseline"] = {"value": cnt / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {cnt} RR sets of the step-0 solve's stream, sampling only "
+                                          f"({dt:.1f} s single-threaded)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.free()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

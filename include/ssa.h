@@ -1,0 +1,216 @@
+/*
+ * ssa.h -- C ABI of the GB300 Stop-and-Stare library (libssa.so).
+ *
+ * Influence maximisation by reverse influence sampling with the SSA and D-SSA
+ * stopping rules of Nguyen, Thai, Dinh, "Stop-and-Stare: Optimal Sampling
+ * Algorithms for Viral Marketing in Billion-scale Networks" (arXiv 1605.07990).
+ * Every compute step runs in the library's own sm_103a CUDA kernels; the host
+ * side only evaluates the FP64 stopping rules from integer counts.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an ssa_status and never aborts the process.  On an
+ *     error, ssa_last_error() gives a one-line message for the calling thread.
+ *   - Pointers documented as "host" are plain host memory owned by the caller;
+ *     the library copies what it needs before returning (except where noted).
+ *     Pointers documented as "device" are CUDA device pointers on the current
+ *     device.  Outputs are caller-allocated.
+ *   - Graph, pool and solver objects are opaque and owned by the library; they
+ *     live on the CUDA device that was current when they were created.
+ *   - Node ids are int32 in [0, n); sample ids are int64.
+ *   - Randomness is Philox4x32-10 keyed by (seed; purpose, stream, sample id,
+ *     edge or node id), so every RR set is a pure function of its key and is
+ *     independent of batch size, launch shape and traversal order:
+ *       key     = (lo32(seed), hi32(seed))
+ *       counter = (lo32(x), hi32(x), lo32(j), purpose<<28 | stream<<20 | (j>>32 & 0xFFFFF))
+ *       purposes ROOT=1 (x=0), IC=2 (x=e>>2, output word e&3), LT=3 (x=v, word 0),
+ *                WEIGHT=5 (x=e, j=0, stream=0)
+ *     where j is the sample id, e the CSR position of an in-edge and v a node.
+ */
+#ifndef SSA_H
+#define SSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SSA_OK = 0,
+  SSA_E_ARG = 1,        /* bad argument (null pointer, out-of-range id or size) */
+  SSA_E_NOMEM = 2,      /* device or host allocation failed */
+  SSA_E_POOL_FULL = 3,  /* the RR pool would exceed its byte cap before a stop */
+  SSA_E_CUDA = 4,       /* a CUDA runtime call failed */
+  SSA_E_TIMEOUT = 5,    /* a bounded device wait gave up (kernel returned, context kept) */
+  SSA_E_CANCELLED = 6,  /* serving: request cancelled */
+  SSA_E_INTERNAL = 7,   /* internal invariant broken (a bug) */
+  SSA_E_NOT_READY = 8   /* serving: result not ready yet */
+} ssa_status;
+
+typedef enum { SSA_IC = 0, SSA_LT = 1 } ssa_model;   /* Sec. 2.1 */
+typedef enum { SSA_ALGO_SSA = 0, SSA_ALGO_DSSA = 1 } ssa_algo;
+
+/* Edge weights w(u,v) (Sec. 2), held per in-edge as a uint32 threshold t:
+ * the edge is live in a sample when its keyed 32-bit draw r satisfies r < t,
+ * and t = 0xFFFFFFFF means probability exactly 1.
+ *   SSA_W_WC          w = 1/d_in(v) (Sec. 6.1): t = floor(2^32/d_in), d_in=1 -> 0xFFFFFFFF
+ *   SSA_W_TRIVALENCY  w drawn uniformly from {0.1, 0.01, 0.001} by the keyed
+ *                     WEIGHT draw of the edge's CSR position: index floor(3 r / 2^32),
+ *                     t = floor(2^32 w) = 429496729, 42949672, 4294967
+ *   SSA_W_EXPLICIT    t given per input edge
+ * LT (Sec. 2.1) needs SSA_W_WC: each visited node keeps the in-edge of index
+ * floor(r d_in / 2^32) of its in-list, r its keyed LT draw. */
+typedef enum { SSA_W_WC = 0, SSA_W_TRIVALENCY = 1, SSA_W_EXPLICIT = 2 } ssa_weighting;
+
+typedef struct ssa_graph ssa_graph;
+typedef struct ssa_pool ssa_pool;
+typedef struct ssa_solver ssa_solver;
+
+const char* ssa_status_str(ssa_status s);
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to len) into buf.  Returns SSA_OK. */
+ssa_status ssa_last_error(char* buf, size_t len);
+/* Library version string, e.g. "ssa-gb300 0.1 sm_103a". */
+const char* ssa_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Graph store (Sec. 2: G = (V, E, w)).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Build the device-resident in-edge CSR of a directed graph.
+ *   n, m        node and edge counts (1 <= n < 2^31, 0 <= m < 2^31)
+ *   src, dst    host int32[m]: edge i is (src[i] -> dst[i]); any order;
+ *               duplicates are parallel edges, self-loops are kept
+ *   thr         host uint32[m] thresholds for SSA_W_EXPLICIT, else NULL
+ *   weighting   see ssa_weighting
+ *   weight_seed key of the trivalency draw
+ *   out         receives the graph handle
+ * Each node's in-list is ordered by (src, input position); that order fixes
+ * the CSR position e that keys the IC coin of an edge.  The arrays are copied;
+ * the caller keeps ownership.  Errors: SSA_E_ARG (ids out of range, null
+ * arrays, LT-incompatible request), SSA_E_NOMEM, SSA_E_CUDA. */
+ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                          const uint32_t* thr, ssa_weighting weighting, uint64_t weight_seed,
+                          ssa_graph** out);
+ssa_status ssa_free_graph(ssa_graph* g);
+/* n, m and device bytes held by the graph (any pointer may be NULL). */
+ssa_status ssa_graph_info(const ssa_graph* g, int64_t* n, int64_t* m, int64_t* device_bytes);
+/* Copy the CSR back to host arrays: off int64[n+1], src int32[m], thr uint32[m]
+ * (any may be NULL). */
+ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint32_t* thr);
+
+/* ------------------------------------------------------------------------ */
+/* Solve (Definition 1: IM; Algorithm 1 SSA; Algorithm 4 D-SSA).            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  ssa_algo algo;
+  ssa_model model;
+  int32_t k;                 /* 1 <= k <= n */
+  double eps;                /* 0 < eps < 1 - 1/e */
+  double delta;              /* 0 < delta < 1 (the paper's experiments use 1/n) */
+  uint64_t seed;             /* Philox key */
+  const uint32_t* benefit;   /* host uint32[n] WRIS benefits (Sec. 6.3.1), or NULL for
+                                uniform sources; copied during the call */
+  int64_t pool_bytes_cap;    /* RR-pool cap in bytes (0 = library default) */
+} ssa_params;
+
+/* One stop-and-stare round. */
+typedef struct {
+  int32_t t;                 /* round number, from 1 */
+  int32_t stop;              /* 1 on the round that returned */
+  int64_t n_sets;            /* |R_t| = ceil(Lambda) * 2^(t-1) */
+  int64_t cov;               /* Cov_{R_t}(S_t) from Max-Coverage */
+  int64_t check_cov;         /* D-SSA: Cov_{R^c_t}(S_t); SSA: Estimate-Inf successes; -1 if not run */
+  int64_t check_T;           /* SSA: Estimate-Inf T (0: T_max reached or not run) */
+  double stat;               /* D-SSA: eps_t (-1 if D1 failed); SSA: I_c (-1 if none) */
+} ssa_round;
+
+/* Kernel classes timed with CUDA events when ssa_result.kstats is requested. */
+enum {
+  SSA_K_SAMPLE_WARP = 0,     /* RR sampler, warp-per-sample tier */
+  SSA_K_SAMPLE_CTA = 1,      /* RR sampler, CTA-per-sample tier (large sets) */
+  SSA_K_INDEX = 2,           /* node -> set index build (count, scan, scatter) */
+  SSA_K_GREEDY = 3,          /* Max-Coverage argmax + cover steps */
+  SSA_K_STARE = 4,           /* Cov over R^c_t, Estimate-Inf first-T search */
+  SSA_K_COUNT = 5
+};
+
+typedef struct {
+  int64_t launches;          /* kernel launches of this class */
+  double ms;                 /* summed CUDA-event time of those launches */
+} ssa_kstat;
+
+typedef struct {
+  int32_t* seeds;            /* in: host int32[k] buffer; out: the seed set S_k */
+  ssa_round* trace;          /* in: host ssa_round[trace_cap] buffer or NULL */
+  int32_t trace_cap;
+  /* outputs */
+  double influence;          /* scale * Cov_R(S)/|R| at the returned round; scale = n,
+                                or the benefit total W for WRIS */
+  int32_t rounds;
+  int64_t n_rr;              /* RR sets generated (Estimate-Inf included) */
+  int64_t pool_entries;      /* RR-pool entries stored (sum of |R_j|) */
+  int64_t edge_visits;       /* in-edges examined (IC) / in-neighbour picks (LT) */
+  int64_t node_visits;       /* nodes added to RR sets (Estimate-Inf included) */
+  int64_t cta_sets;          /* RR sets finished by the CTA-per-sample sampler tier */
+  int64_t cta_edge_visits;   /* that tier's share of edge_visits */
+  int64_t cta_node_visits;   /* that tier's share of node_visits */
+  int64_t kernel_launches;   /* CUDA kernels this library launched for the solve */
+  double seconds;            /* host wall time of the call */
+  int32_t want_kstats;       /* in: 1 to time kernel classes with CUDA events */
+  ssa_kstat kstats[SSA_K_COUNT];
+} ssa_result;
+
+/* One-shot solve: creates a solver, runs, frees it.  Errors: SSA_E_ARG,
+ * SSA_E_NOMEM, SSA_E_POOL_FULL, SSA_E_CUDA, SSA_E_TIMEOUT. */
+ssa_status ssa_solve(const ssa_graph* g, const ssa_params* p, ssa_result* out);
+
+/* A solver keeps device workspaces (RR pool, index, scratch) and a CUDA stream
+ * across solves on one graph.  stream: a cudaStream_t to run on, or NULL for a
+ * library-created one.  pool_bytes_cap: cap for the RR pool (0 = 60% of the
+ * device memory free at creation). */
+ssa_status ssa_solver_create(const ssa_graph* g, void* stream, int64_t pool_bytes_cap, ssa_solver** out);
+ssa_status ssa_solver_solve(ssa_solver* s, const ssa_params* p, ssa_result* out);
+ssa_status ssa_solver_free(ssa_solver* s);
+
+/* ------------------------------------------------------------------------ */
+/* Hot-path steps, one entry point each (parity tests call these).          */
+/* ------------------------------------------------------------------------ */
+
+/* An RR pool: the RR sets of samples [0, count) of one (model, seed, stream)
+ * (Definition 2), stored on the device as flat (node, sample) entries.
+ * benefit: host uint32[n] WRIS weights or NULL (copied).  */
+ssa_status ssa_pool_create(const ssa_graph* g, ssa_model model, uint64_t seed, uint32_t stream,
+                           const uint32_t* benefit, ssa_pool** out);
+ssa_status ssa_pool_free(ssa_pool* p);
+/* Sample until the pool holds `count` sets (new samples [old count, count)). */
+ssa_status ssa_pool_grow(ssa_pool* p, int64_t count);
+ssa_status ssa_pool_info(const ssa_pool* p, int64_t* count, int64_t* entries, int64_t* edge_visits);
+/* Copy sets [first, first+count) to host: off int64[count+1] (off[0] = 0),
+ * nodes int32[cap].  Nodes of one set come in traversal order (not sorted).
+ * SSA_E_ARG if cap is too small (off is still filled). */
+ssa_status ssa_pool_export(const ssa_pool* p, int64_t first, int64_t count, int64_t* off,
+                           int32_t* nodes, int64_t cap);
+/* Node -> set index over sets [0, N): cnt int32[n] (host) = #sets holding v. */
+ssa_status ssa_pool_counts(ssa_pool* p, int64_t N, int32_t* cnt);
+/* Max-Coverage (Algorithm 2) over sets [0, N): k picks of largest marginal
+ * gain, ties to the smallest id, seeds never re-picked.  seeds int32[k],
+ * gains int64[k] (host); *cov = Cov_R(S). */
+ssa_status ssa_max_coverage(ssa_pool* p, int64_t N, int32_t k, int32_t* seeds, int64_t* gains,
+                            int64_t* cov);
+/* Cov (Eq. 1) of the host seed list over sets [first, first+count). */
+ssa_status ssa_coverage(ssa_pool* p, int64_t first, int64_t count, const int32_t* seeds, int32_t k,
+                        int64_t* cov);
+/* Estimate-Inf (Algorithm 3): RR sets j = 0, 1, ... of `stream`, first T with
+ * #{j < T : R_j meets S} >= lambda2, T <= t_max.  *T = 0 when t_max sets do
+ * not reach it (the paper's -1); *hits = successes counted up to T (or t_max). */
+ssa_status ssa_estimate_inf(const ssa_graph* g, ssa_model model, uint64_t seed, uint32_t stream,
+                            const uint32_t* benefit, const int32_t* seeds, int32_t k, double lambda2,
+                            int64_t t_max, int64_t* T, int64_t* hits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSA_H */

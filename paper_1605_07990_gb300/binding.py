@@ -1,0 +1,346 @@
+"""Thin ctypes binding of libssa (include/ssa.h): the same entry-point names,
+argument marshalling only.  Every compute step runs in the library's CUDA
+kernels; there is no CPU fallback -- loading fails loudly when libssa.so is
+missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libssa.so")
+
+SSA_OK = 0
+SSA_IC, SSA_LT = 0, 1
+SSA_ALGO_SSA, SSA_ALGO_DSSA = 0, 1
+SSA_W_WC, SSA_W_TRIVALENCY, SSA_W_EXPLICIT = 0, 1, 2
+KERNEL_CLASSES = ["sample_warp", "sample_cta", "index", "greedy", "stare"]
+
+STATUS = {0: "SSA_OK", 1: "SSA_E_ARG", 2: "SSA_E_NOMEM", 3: "SSA_E_POOL_FULL", 4: "SSA_E_CUDA",
+          5: "SSA_E_TIMEOUT", 6: "SSA_E_CANCELLED", 7: "SSA_E_INTERNAL", 8: "SSA_E_NOT_READY"}
+
+
+class SSAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ssa_params(C.Structure):
+    _fields_ = [("algo", C.c_int), ("model", C.c_int), ("k", C.c_int32), ("eps", C.c_double),
+                ("delta", C.c_double), ("seed", C.c_uint64), ("benefit", C.c_void_p),
+                ("pool_bytes_cap", C.c_int64)]
+
+
+class ssa_round(C.Structure):
+    _fields_ = [("t", C.c_int32), ("stop", C.c_int32), ("n_sets", C.c_int64), ("cov", C.c_int64),
+                ("check_cov", C.c_int64), ("check_T", C.c_int64), ("stat", C.c_double)]
+
+
+class ssa_kstat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double)]
+
+
+class ssa_result(C.Structure):
+    _fields_ = [("seeds", C.c_void_p), ("trace", C.c_void_p), ("trace_cap", C.c_int32),
+                ("influence", C.c_double), ("rounds", C.c_int32), ("n_rr", C.c_int64),
+                ("pool_entries", C.c_int64), ("edge_visits", C.c_int64), ("node_visits", C.c_int64),
+                ("cta_sets", C.c_int64), ("cta_edge_visits", C.c_int64), ("cta_node_visits", C.c_int64),
+                ("kernel_launches", C.c_int64), ("seconds", C.c_double), ("want_kstats", C.c_int32),
+                ("kstats", ssa_kstat * 5)]
+
+
+EXPORTS = {
+    "ssa_status_str": (C.c_char_p, [C.c_int]),
+    "ssa_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "ssa_version": (C.c_char_p, []),
+    "ssa_load_graph": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_uint64,
+                                 C.POINTER(C.c_void_p)]),
+    "ssa_free_graph": (C.c_int, [C.c_void_p]),
+    "ssa_graph_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ssa_graph_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
+    "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
+    "ssa_solver_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
+    "ssa_solver_free": (C.c_int, [C.c_void_p]),
+    "ssa_pool_create": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
+    "ssa_pool_free": (C.c_int, [C.c_void_p]),
+    "ssa_pool_grow": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ssa_pool_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ssa_pool_export": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64]),
+    "ssa_pool_counts": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "ssa_max_coverage": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ssa_coverage": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ssa_estimate_inf": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
+                                   C.c_int32, C.c_double, C.c_int64, C.c_void_p, C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libssa.so (raises OSError when the extension is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libssa.so not built at {LIB_PATH}: run paper_1605_07990_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != SSA_OK:
+        buf = C.create_string_buffer(512)
+        lib().ssa_last_error(buf, 512)
+        raise SSAError(status, buf.value.decode(errors="replace"))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _u64(x):
+    return int(x) & 0xFFFFFFFFFFFFFFFF
+
+
+def ssa_version() -> str:
+    return lib().ssa_version().decode()
+
+
+# ---- graph ----
+class Graph:
+    """Opaque device-resident graph handle (ssa_graph*)."""
+
+    def __init__(self, handle, n, m):
+        self.h, self.n, self.m = handle, n, m
+
+    def free(self):
+        if self.h:
+            _check(lib().ssa_free_graph(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ssa_load_graph(n, src, dst, thr=None, weighting=SSA_W_WC, weight_seed=1) -> Graph:
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    thr = None if thr is None else np.ascontiguousarray(thr, dtype=np.uint32)
+    h = C.c_void_p()
+    _check(lib().ssa_load_graph(int(n), int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(thr), int(weighting),
+                                _u64(weight_seed), C.byref(h)))
+    return Graph(h.value, int(n), int(src.shape[0]))
+
+
+def ssa_free_graph(g: Graph):
+    g.free()
+
+
+def ssa_graph_info(g: Graph):
+    n, m, b = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().ssa_graph_info(g.h, C.byref(n), C.byref(m), C.byref(b)))
+    return n.value, m.value, b.value
+
+
+def ssa_graph_export(g: Graph):
+    off = np.zeros(g.n + 1, dtype=np.int64)
+    src = np.zeros(max(g.m, 1), dtype=np.int32)
+    thr = np.zeros(max(g.m, 1), dtype=np.uint32)
+    _check(lib().ssa_graph_export(g.h, _ptr(off), _ptr(src), _ptr(thr)))
+    return off, src[:g.m], thr[:g.m]
+
+
+# ---- solve ----
+@dataclass
+class Result:
+    seeds: np.ndarray
+    influence: float
+    rounds: int
+    n_rr: int
+    pool_entries: int
+    edge_visits: int
+    node_visits: int
+    kernel_launches: int
+    seconds: float
+    cta_sets: int = 0
+    cta_edge_visits: int = 0
+    cta_node_visits: int = 0
+    trace: list = field(default_factory=list)
+    kstats: dict = field(default_factory=dict)
+
+
+def _params(algo, model, k, eps, delta, seed, benefit, pool_bytes_cap):
+    p = ssa_params()
+    p.algo, p.model, p.k, p.eps, p.delta, p.seed = int(algo), int(model), int(k), float(eps), float(delta), _u64(seed)
+    p.benefit = _ptr(benefit)
+    p.pool_bytes_cap = int(pool_bytes_cap)
+    return p
+
+
+def _result(k, trace_cap, want_kstats):
+    seeds = np.zeros(k, dtype=np.int32)
+    tr = (ssa_round * trace_cap)()
+    r = ssa_result()
+    r.seeds = seeds.ctypes.data
+    r.trace = C.cast(tr, C.c_void_p)
+    r.trace_cap = trace_cap
+    r.want_kstats = int(bool(want_kstats))
+    return r, seeds, tr
+
+
+def _unpack(r, seeds, tr):
+    trace = [{"t": x.t, "stop": x.stop, "n_sets": x.n_sets, "cov": x.cov, "check_cov": x.check_cov,
+              "check_T": x.check_T, "stat": x.stat} for x in tr[:min(r.rounds, r.trace_cap)]]
+    ks = {KERNEL_CLASSES[i]: {"launches": r.kstats[i].launches, "ms": r.kstats[i].ms} for i in range(5)}
+    return Result(seeds.copy(), r.influence, r.rounds, r.n_rr, r.pool_entries, r.edge_visits, r.node_visits,
+                  r.kernel_launches, r.seconds, r.cta_sets, r.cta_edge_visits, r.cta_node_visits, trace, ks)
+
+
+def ssa_solve(g: Graph, algo, model, k, eps, delta, seed, benefit=None, pool_bytes_cap=0, want_kstats=False,
+              trace_cap=64) -> Result:
+    b = None if benefit is None else np.ascontiguousarray(benefit, dtype=np.uint32)
+    p = _params(algo, model, k, eps, delta, seed, b, pool_bytes_cap)
+    r, seeds, tr = _result(k, trace_cap, want_kstats)
+    _check(lib().ssa_solve(g.h, C.byref(p), C.byref(r)))
+    return _unpack(r, seeds, tr)
+
+
+class Solver:
+    """ssa_solver*: device workspaces and a stream reused across solves."""
+
+    def __init__(self, g: Graph, stream=None, pool_bytes_cap=0):
+        h = C.c_void_p()
+        _check(lib().ssa_solver_create(g.h, stream, int(pool_bytes_cap), C.byref(h)))
+        self.h, self.g = h.value, g
+
+    def solve(self, algo, model, k, eps, delta, seed, benefit=None, pool_bytes_cap=0, want_kstats=False,
+              trace_cap=64) -> Result:
+        b = None if benefit is None else np.ascontiguousarray(benefit, dtype=np.uint32)
+        p = _params(algo, model, k, eps, delta, seed, b, pool_bytes_cap)
+        r, seeds, tr = _result(k, trace_cap, want_kstats)
+        _check(lib().ssa_solver_solve(self.h, C.byref(p), C.byref(r)))
+        return _unpack(r, seeds, tr)
+
+    def free(self):
+        if self.h:
+            _check(lib().ssa_solver_free(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ssa_solver_create(g, stream=None, pool_bytes_cap=0) -> Solver:
+    return Solver(g, stream, pool_bytes_cap)
+
+
+def ssa_solver_solve(s: Solver, *a, **kw) -> Result:
+    return s.solve(*a, **kw)
+
+
+def ssa_solver_free(s: Solver):
+    s.free()
+
+
+# ---- pools ----
+class Pool:
+    """ssa_pool*: RR sets of samples [0, count) of one (model, seed, stream)."""
+
+    def __init__(self, g: Graph, model=SSA_IC, seed=1, stream=0, benefit=None):
+        b = None if benefit is None else np.ascontiguousarray(benefit, dtype=np.uint32)
+        h = C.c_void_p()
+        _check(lib().ssa_pool_create(g.h, int(model), _u64(seed), int(stream), _ptr(b), C.byref(h)))
+        self.h, self.g = h.value, g
+
+    def free(self):
+        if self.h:
+            _check(lib().ssa_pool_free(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def grow(self, count):
+        _check(lib().ssa_pool_grow(self.h, int(count)))
+        return self
+
+    def info(self):
+        c, e, ev = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().ssa_pool_info(self.h, C.byref(c), C.byref(e), C.byref(ev)))
+        return c.value, e.value, ev.value
+
+    def export(self, first=0, count=None):
+        total = self.info()[0]
+        count = total - first if count is None else count
+        off = np.zeros(count + 1, dtype=np.int64)
+        cap = self.info()[1]
+        nodes = np.zeros(max(cap, 1), dtype=np.int32)
+        _check(lib().ssa_pool_export(self.h, int(first), int(count), _ptr(off), _ptr(nodes), int(cap)))
+        return off, nodes[:off[-1]]
+
+    def sets(self, first=0, count=None, sort=True):
+        off, nodes = self.export(first, count)
+        out = [nodes[off[i]:off[i + 1]] for i in range(len(off) - 1)]
+        return [np.sort(x) for x in out] if sort else out
+
+    def counts(self, N):
+        cnt = np.zeros(self.g.n, dtype=np.int32)
+        _check(lib().ssa_pool_counts(self.h, int(N), _ptr(cnt)))
+        return cnt
+
+    def max_coverage(self, N, k):
+        seeds = np.zeros(k, dtype=np.int32)
+        gains = np.zeros(k, dtype=np.int64)
+        cov = C.c_int64()
+        _check(lib().ssa_max_coverage(self.h, int(N), int(k), _ptr(seeds), _ptr(gains), C.byref(cov)))
+        return seeds, gains, cov.value
+
+    def coverage(self, first, count, S):
+        S = np.ascontiguousarray(S, dtype=np.int32)
+        cov = C.c_int64()
+        _check(lib().ssa_coverage(self.h, int(first), int(count), _ptr(S), int(S.shape[0]), C.byref(cov)))
+        return cov.value
+
+
+def ssa_pool_create(g, model=SSA_IC, seed=1, stream=0, benefit=None) -> Pool:
+    return Pool(g, model, seed, stream, benefit)
+
+
+def ssa_pool_grow(p: Pool, count):
+    return p.grow(count)
+
+
+def ssa_max_coverage(p: Pool, N, k):
+    return p.max_coverage(N, k)
+
+
+def ssa_coverage(p: Pool, first, count, S):
+    return p.coverage(first, count, S)
+
+
+def ssa_estimate_inf(g: Graph, model, seed, stream, S, lambda2, t_max, benefit=None):
+    b = None if benefit is None else np.ascontiguousarray(benefit, dtype=np.uint32)
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    T, hits = C.c_int64(), C.c_int64()
+    _check(lib().ssa_estimate_inf(g.h, int(model), _u64(seed), int(stream), _ptr(b), _ptr(S), int(S.shape[0]),
+                                  float(lambda2), int(t_max), C.byref(T), C.byref(hits)))
+    return T.value, hits.value

@@ -1,0 +1,1060 @@
+// C ABI of libssa (include/ssa.h) and the host side of the Stop-and-Stare
+// drivers: device workspaces, sampling batches, and the FP64 stopping rules of
+// SSA (Algorithm 1) and D-SSA (Algorithm 4) evaluated from integer counts.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <chrono>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ssa.h"
+#include "kernels.h"
+
+using namespace ssa;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+namespace {
+thread_local char g_err[512] = "";
+
+ssa_status fail(ssa_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? SSA_E_NOMEM : SSA_E_CUDA, "%s failed: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                             \
+    }                                                                                             \
+  } while (0)
+
+#define TRY(call)                   \
+  do {                              \
+    ssa_status s_ = (call);         \
+    if (s_ != SSA_OK) return s_;    \
+  } while (0)
+
+template <typename T>
+ssa_status dev_alloc(T** p, size_t count, cudaStream_t st) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  CU(cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * count, st));
+  return SSA_OK;
+}
+
+template <typename T>
+void dev_free(T*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+}
+
+// Grow a device array to `want` elements keeping the first `keep`.
+template <typename T>
+ssa_status dev_grow(T** p, int64_t* cap, int64_t want, int64_t keep, cudaStream_t st) {
+  if (want <= *cap) return SSA_OK;
+  T* q = nullptr;
+  TRY(dev_alloc(&q, (size_t)want, st));
+  if (*p && keep > 0) CU(cudaMemcpyAsync(q, *p, sizeof(T) * (size_t)keep, cudaMemcpyDeviceToDevice, st));
+  if (*p) cudaFreeAsync(*p, st);
+  *p = q;
+  *cap = want;
+  return SSA_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// graph
+// ---------------------------------------------------------------------------
+struct ssa_graph {
+  int device = 0;
+  int64_t n = 0, m = 0;
+  int weighting = 0;
+  int64_t* off = nullptr;
+  uint2* edge = nullptr;
+  int64_t bytes = 0;
+  GraphView view() const {
+    GraphView v;
+    v.n = n;
+    v.m = m;
+    v.off = off;
+    v.edge = edge;
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// per-stream execution context: kernel counting and optional event timing
+// ---------------------------------------------------------------------------
+namespace {
+struct Exec {
+  cudaStream_t st = nullptr;
+  int num_sms = 152;
+  int64_t launches = 0;
+  bool timing = false;
+  struct Ev {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> evs;
+  std::vector<cudaEvent_t> spare;
+
+  cudaEvent_t take() {
+    if (!spare.empty()) {
+      cudaEvent_t e = spare.back();
+      spare.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // begin/end a timed region of one kernel class
+  int begin(int cls) {
+    if (!timing) return -1;
+    Ev e{cls, take(), take()};
+    cudaEventRecord(e.a, st);
+    evs.push_back(e);
+    return (int)evs.size() - 1;
+  }
+  void end(int h) {
+    if (h >= 0) cudaEventRecord(evs[(size_t)h].b, st);
+  }
+  void collect(ssa_kstat* ks) {
+    for (auto& e : evs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess && ks) {
+        ks[e.cls].launches += 1;
+        ks[e.cls].ms += ms;
+      }
+      spare.push_back(e.a);
+      spare.push_back(e.b);
+    }
+    evs.clear();
+  }
+  ~Exec() {
+    for (auto& e : evs) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    for (auto e : spare) cudaEventDestroy(e);
+  }
+};
+
+// The RR pool: flat (node, sample) entries in batch order plus per-sample
+// extents; `bounds` records (sets, entries) after every batch so that the
+// sets [0, N) of a batch boundary N are exactly the entries [0, E(N)).
+struct DevPool {
+  int64_t cap_entries = 0, cap_sets = 0;
+  int32_t* nodes = nullptr;
+  int32_t* samp = nullptr;
+  int64_t* set_start = nullptr;
+  int32_t* set_len = nullptr;
+  int64_t count = 0, entries = 0;
+  std::vector<std::pair<int64_t, int64_t>> bounds{{0, 0}};
+  int64_t byte_cap = 0;
+
+  int64_t bytes_for(int64_t ents, int64_t sets) const { return ents * 12 + sets * 14; }
+  // entries range covering samples [a, b)
+  void entry_range(int64_t a, int64_t b, int64_t* e0, int64_t* e1) const {
+    *e0 = 0;
+    *e1 = entries;
+    for (auto& p : bounds) {
+      if (p.first <= a) *e0 = p.second;
+      if (p.first >= b) {
+        *e1 = p.second;
+        break;
+      }
+    }
+  }
+  void release(cudaStream_t st) {
+    dev_free(nodes, st);
+    dev_free(samp, st);
+    dev_free(set_start, st);
+    dev_free(set_len, st);
+    cap_entries = cap_sets = 0;
+  }
+};
+
+// Sampling state: counters, CTA-tier hand-off list and scratch, seed bits.
+struct Sampler {
+  GraphView g;
+  int model = 0;
+  LaunchCfg cfg;
+  Counters* d_ctr = nullptr;
+  Counters* h_ctr = nullptr;  // pinned
+  int64_t* big_list = nullptr;
+  int64_t big_cap = 0;
+  uint32_t* slot_bitmap = nullptr;
+  int32_t* slot_queue = nullptr;
+  uint8_t* hit = nullptr;
+  int64_t hit_cap = 0;
+  uint32_t* seed_bits = nullptr;
+  uint64_t* bprefix = nullptr;
+  uint64_t wsum = 0;
+  int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
+  int64_t cta_edge_visits = 0, cta_node_visits = 0, cta_samples = 0;
+
+  void tally(int64_t count) {
+    edge_visits += (int64_t)h_ctr->edge_visits;
+    node_visits += (int64_t)h_ctr->node_visits;
+    cta_edge_visits += (int64_t)h_ctr->cta_edge_visits;
+    cta_node_visits += (int64_t)h_ctr->cta_node_visits;
+    cta_samples += (int64_t)h_ctr->big_count;
+    samples += count;
+  }
+
+  ssa_status init(const ssa_graph* G, int mdl, const uint32_t* benefit, Exec& X) {
+    g = G->view();
+    model = mdl;
+    cfg = sampler_config(g, mdl);
+    X.num_sms = cfg.num_sms;
+    TRY(dev_alloc(&d_ctr, 1, X.st));
+    CU(cudaMallocHost(reinterpret_cast<void**>(&h_ctr), sizeof(Counters)));
+    const int64_t words = (g.n + 31) / 32;
+    TRY(dev_alloc(&slot_queue, (size_t)g.n * (size_t)cfg.cta_blocks, X.st));
+    if (!cfg.cta_smem_bitmap) {
+      TRY(dev_alloc(&slot_bitmap, (size_t)words * (size_t)cfg.cta_blocks, X.st));
+      CU(cudaMemsetAsync(slot_bitmap, 0, sizeof(uint32_t) * (size_t)words * (size_t)cfg.cta_blocks, X.st));
+    }
+    TRY(dev_alloc(&seed_bits, (size_t)words, X.st));
+    if (benefit) {
+      std::vector<uint64_t> pre((size_t)g.n + 1, 0);
+      for (int64_t v = 0; v < g.n; ++v) pre[(size_t)v + 1] = pre[(size_t)v] + benefit[v];
+      wsum = pre[(size_t)g.n];
+      if (wsum == 0) return fail(SSA_E_ARG, "benefit weights sum to zero");
+      TRY(dev_alloc(&bprefix, (size_t)g.n + 1, X.st));
+      CU(cudaMemcpyAsync(bprefix, pre.data(), sizeof(uint64_t) * pre.size(), cudaMemcpyHostToDevice, X.st));
+      CU(cudaStreamSynchronize(X.st));
+    }
+    return SSA_OK;
+  }
+  void release(cudaStream_t st) {
+    dev_free(d_ctr, st);
+    if (h_ctr) cudaFreeHost(h_ctr);
+    h_ctr = nullptr;
+    dev_free(big_list, st);
+    dev_free(slot_bitmap, st);
+    dev_free(slot_queue, st);
+    dev_free(hit, st);
+    dev_free(seed_bits, st);
+    dev_free(bprefix, st);
+  }
+
+  SampleJob job(uint64_t seed, uint32_t stream, int64_t j0, int64_t count) const {
+    SampleJob J;
+    J.g = g;
+    J.model = model;
+    J.seed = seed;
+    J.stream = stream;
+    J.j0 = j0;
+    J.count = count;
+    J.bprefix = bprefix;
+    J.big_list = big_list;
+    J.slot_bitmap = slot_bitmap;
+    J.slot_queue = slot_queue;
+    J.bitmap_words = (g.n + 31) / 32;
+    J.ctr = d_ctr;
+    return J;
+  }
+
+  ssa_status run(SampleJob& J, Exec& X, unsigned long long cursor0) {
+    std::memset(h_ctr, 0, sizeof(Counters));
+    h_ctr->cursor = cursor0;
+    CU(cudaMemcpyAsync(d_ctr, h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, X.st));
+    int h = X.begin(SSA_K_SAMPLE_WARP);
+    CU(launch_sample_warp(J, cfg, X.st));
+    X.end(h);
+    h = X.begin(SSA_K_SAMPLE_CTA);
+    CU(launch_sample_cta(J, cfg, X.st));
+    X.end(h);
+    X.launches += 2;
+    CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, X.st));
+    CU(cudaStreamSynchronize(X.st));
+    if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error");
+    return SSA_OK;
+  }
+
+  // Append samples [pool.count, pool.count + count) of (seed, stream) to the pool.
+  ssa_status append(DevPool& P, uint64_t seed, uint32_t stream, int64_t count, Exec& X) {
+    if (count <= 0) return SSA_OK;
+    const int64_t j0 = P.count;
+    if (j0 + count > (int64_t)0x7FFFFFFF) return fail(SSA_E_POOL_FULL, "more than 2^31 RR sets");
+    TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    if (j0 + count > P.cap_sets) {
+      int64_t want = std::max<int64_t>(j0 + count, P.cap_sets * 2);
+      int64_t c1 = P.cap_sets, c2 = P.cap_sets;
+      TRY(dev_grow(&P.set_start, &c1, want, j0, X.st));
+      TRY(dev_grow(&P.set_len, &c2, want, j0, X.st));
+      P.cap_sets = want;
+    }
+    if (P.cap_entries == 0) {
+      int64_t want = std::max<int64_t>(1 << 20, count * 16);
+      if (P.byte_cap > 0) want = std::max<int64_t>(1, std::min<int64_t>(want, (P.byte_cap - P.cap_sets * 14) / 12));
+      int64_t a = 0, b = 0;
+      TRY(dev_grow(&P.nodes, &a, want, 0, X.st));
+      TRY(dev_grow(&P.samp, &b, want, 0, X.st));
+      P.cap_entries = want;
+    }
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      SampleJob J = job(seed, stream, j0, count);
+      J.mode = MODE_STORE;
+      J.pool_nodes = P.nodes;
+      J.pool_samp = P.samp;
+      J.pool_cap = P.cap_entries;
+      J.set_start = P.set_start;
+      J.set_len = P.set_len;
+      TRY(run(J, X, (unsigned long long)P.entries));
+      if (!h_ctr->pool_overflow) break;
+      // the cursor kept counting past the cap: grow to what the batch needs and redo it
+      const int64_t need = (int64_t)h_ctr->cursor;
+      int64_t want = std::max<int64_t>(need + need / 4, P.cap_entries * 2);
+      if (P.byte_cap > 0 && P.bytes_for(want, P.cap_sets) > P.byte_cap) {
+        want = need;
+        if (P.bytes_for(want, P.cap_sets) > P.byte_cap)
+          return fail(SSA_E_POOL_FULL, "RR pool needs %lld entries, over the %lld-byte cap", (long long)need,
+                      (long long)P.byte_cap);
+      }
+      int64_t a = P.cap_entries, b = P.cap_entries;
+      TRY(dev_grow(&P.nodes, &a, want, P.entries, X.st));
+      TRY(dev_grow(&P.samp, &b, want, P.entries, X.st));
+      P.cap_entries = want;
+    }
+    if (h_ctr->pool_overflow) return fail(SSA_E_INTERNAL, "pool growth did not converge");
+    tally(count);
+    P.entries = (int64_t)h_ctr->cursor;
+    P.count = j0 + count;
+    P.bounds.emplace_back(P.count, P.entries);
+    return SSA_OK;
+  }
+
+  // Hit-test batch (Estimate-Inf): hit[i] = R_{j0+i} meets the seed bits.
+  ssa_status hits(uint64_t seed, uint32_t stream, int64_t j0, int64_t count, Exec& X) {
+    TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&hit, &hit_cap, count, 0, X.st));
+    SampleJob J = job(seed, stream, j0, count);
+    J.mode = MODE_HIT;
+    J.seed_bits = seed_bits;
+    J.hit = hit;
+    TRY(run(J, X, 0));
+    tally(count);
+    hit_samples += count;
+    return SSA_OK;
+  }
+};
+
+// Node -> set index and greedy buffers.
+struct Cover {
+  int64_t n = 0;
+  int64_t n_pad = 0;
+  int32_t* cnt = nullptr;
+  int64_t* inv_off = nullptr;
+  unsigned long long* cur = nullptr;
+  int32_t* inv_samp = nullptr;
+  int64_t inv_cap = 0;
+  void* scan_tmp = nullptr;
+  uint8_t* covered = nullptr;
+  int64_t covered_cap = 0;
+  uint8_t* in_seed = nullptr;
+  unsigned long long* partial = nullptr;
+  int argmax_blocks = 0;
+  int32_t* d_seeds = nullptr;
+  int32_t* d_gains = nullptr;
+  int k_cap = 0;
+  unsigned long long* d_count = nullptr;
+  long long* d_first = nullptr;
+  void* fr_tmp = nullptr;
+  int64_t fr_cap = 0;
+  uint8_t* hitc = nullptr;  // per-sample flags for Cov over a range
+  int64_t hitc_cap = 0;
+
+  ssa_status init(int64_t nn, Exec& X) {
+    n = nn;
+    n_pad = (n + 3) & ~int64_t(3);
+    TRY(dev_alloc(&cnt, (size_t)n_pad, X.st));
+    TRY(dev_alloc(&inv_off, (size_t)n + 1, X.st));
+    TRY(dev_alloc(&cur, (size_t)n + 1, X.st));
+    TRY(dev_alloc(&in_seed, (size_t)n_pad, X.st));
+    CU(cudaMallocAsync(&scan_tmp, scan_tmp_bytes(n), X.st));
+    argmax_blocks = X.num_sms * 4;
+    TRY(dev_alloc(&partial, (size_t)argmax_blocks, X.st));
+    TRY(dev_alloc(&d_count, 1, X.st));
+    TRY(dev_alloc(&d_first, 2, X.st));
+    return SSA_OK;
+  }
+  void release(cudaStream_t st) {
+    dev_free(cnt, st);
+    dev_free(inv_off, st);
+    dev_free(cur, st);
+    dev_free(inv_samp, st);
+    if (scan_tmp) cudaFreeAsync(scan_tmp, st);
+    scan_tmp = nullptr;
+    dev_free(covered, st);
+    dev_free(in_seed, st);
+    dev_free(partial, st);
+    dev_free(d_seeds, st);
+    dev_free(d_gains, st);
+    dev_free(d_count, st);
+    dev_free(d_first, st);
+    if (fr_tmp) cudaFreeAsync(fr_tmp, st);
+    fr_tmp = nullptr;
+    dev_free(hitc, st);
+  }
+
+  // cnt / inv_off / inv_samp over the sets [0, N) of the pool
+  ssa_status build_index(const DevPool& P, int64_t N, Exec& X) {
+    int64_t e0, e1;
+    P.entry_range(0, N, &e0, &e1);
+    const bool exact = (e0 == 0) && [&] {
+      for (auto& b : P.bounds)
+        if (b.first == N) return true;
+      return false;
+    }();
+    TRY(dev_grow(&inv_samp, &inv_cap, std::max<int64_t>(e1, 1), 0, X.st));
+    int h = X.begin(SSA_K_INDEX);
+    CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
+    CU(launch_count_nodes(P.nodes, exact ? nullptr : P.samp, 0, e1, 0, N, cnt, X.st, X.num_sms));
+    int l = 0;
+    CU(launch_exclusive_scan(cnt, n, inv_off, scan_tmp, X.st, &l));
+    CU(cudaMemcpyAsync(cur, inv_off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, X.st));
+    CU(launch_scatter_index(P.nodes, P.samp, 0, e1, 0, N, cur, inv_samp, X.st, X.num_sms));
+    X.end(h);
+    X.launches += 2 + l;
+    return SSA_OK;
+  }
+
+  // Max-Coverage (Algorithm 2) over sets [0, N): seeds/gains to host.
+  ssa_status greedy(const DevPool& P, int64_t N, int k, int32_t* seeds, int64_t* gains, int64_t* cov, Exec& X) {
+    TRY(build_index(P, N, X));
+    if (k > k_cap) {
+      dev_free(d_seeds, X.st);
+      dev_free(d_gains, X.st);
+      TRY(dev_alloc(&d_seeds, (size_t)k, X.st));
+      TRY(dev_alloc(&d_gains, (size_t)k, X.st));
+      k_cap = k;
+    }
+    TRY(dev_grow(&covered, &covered_cap, std::max<int64_t>(N, 1), 0, X.st));
+    int h = X.begin(SSA_K_GREEDY);
+    CU(cudaMemsetAsync(covered, 0, (size_t)std::max<int64_t>(N, 1), X.st));
+    CU(cudaMemsetAsync(in_seed, 0, (size_t)n_pad, X.st));
+    // padding nodes can never be picked
+    if (n_pad > n) CU(cudaMemsetAsync(in_seed + n, 1, (size_t)(n_pad - n), X.st));
+    GreedyBufs b;
+    b.cnt = cnt;
+    b.inv_off = inv_off;
+    b.inv_samp = inv_samp;
+    b.pool_nodes = P.nodes;
+    b.set_start = P.set_start;
+    b.set_len = P.set_len;
+    b.covered = covered;
+    b.in_seed = in_seed;
+    b.partial = partial;
+    b.seeds = d_seeds;
+    b.gains = d_gains;
+    b.n = n;
+    b.argmax_blocks = argmax_blocks;
+    for (int i = 0; i < k; ++i) CU(launch_greedy_step(b, i, X.st, X.num_sms));
+    X.end(h);
+    X.launches += 2 * k;
+    std::vector<int32_t> g32((size_t)k);
+    CU(cudaMemcpyAsync(seeds, d_seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
+    CU(cudaMemcpyAsync(g32.data(), d_gains, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
+    CU(cudaStreamSynchronize(X.st));
+    int64_t c = 0;
+    for (int i = 0; i < k; ++i) {
+      gains[i] = g32[(size_t)i];
+      c += g32[(size_t)i];
+    }
+    *cov = c;
+    return SSA_OK;
+  }
+
+  // Cov (Eq. 1) of the seeds currently flagged in in_seed over sets [a, b).
+  ssa_status coverage_range(const DevPool& P, int64_t a, int64_t b, int64_t* cov, Exec& X) {
+    const int64_t cnt_sets = b - a;
+    if (cnt_sets <= 0) {
+      *cov = 0;
+      return SSA_OK;
+    }
+    int64_t e0, e1;
+    P.entry_range(a, b, &e0, &e1);
+    TRY(dev_grow(&hitc, &hitc_cap, cnt_sets, 0, X.st));
+    int h = X.begin(SSA_K_STARE);
+    CU(cudaMemsetAsync(hitc, 0, (size_t)cnt_sets, X.st));
+    CU(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), X.st));
+    CU(launch_mark_hits(P.nodes, P.samp, e0, e1, in_seed, a, b, hitc, X.st, X.num_sms));
+    CU(launch_count_flags(hitc, cnt_sets, d_count, X.st, X.num_sms));
+    X.end(h);
+    X.launches += 2;
+    unsigned long long c = 0;
+    CU(cudaMemcpyAsync(&c, d_count, sizeof(c), cudaMemcpyDeviceToHost, X.st));
+    CU(cudaStreamSynchronize(X.st));
+    *cov = (int64_t)c;
+    return SSA_OK;
+  }
+};
+
+// Estimate-Inf (Algorithm 3) on the device: hit-test batches of fresh sets
+// of `stream`, then the first T whose prefix of successes reaches `need`.
+ssa_status estimate_inf_dev(Sampler& S, Cover& C, uint64_t seed, uint32_t stream, const int32_t* d_seeds, int k,
+                            int64_t need, int64_t t_max, int64_t first_batch, int64_t* T_out, int64_t* hits_out,
+                            Exec& X) {
+  const int64_t words = (S.g.n + 31) / 32;
+  CU(cudaMemsetAsync(S.seed_bits, 0, sizeof(uint32_t) * (size_t)words, X.st));
+  CU(launch_set_bits(d_seeds, k, S.seed_bits, nullptr, X.st));
+  X.launches += 1;
+  int64_t j = 0, before = 0, B = std::max<int64_t>(first_batch, 4096);
+  *T_out = 0;
+  while (j < t_max) {
+    const int64_t cnt = std::min<int64_t>(B, t_max - j);
+    TRY(S.hits(seed, stream, j, cnt, X));
+    if ((int64_t)first_reach_tmp_bytes(cnt) > C.fr_cap) {
+      if (C.fr_tmp) cudaFreeAsync(C.fr_tmp, X.st);
+      C.fr_cap = (int64_t)first_reach_tmp_bytes(cnt);
+      CU(cudaMallocAsync(&C.fr_tmp, (size_t)C.fr_cap, X.st));
+    }
+    int h = X.begin(SSA_K_STARE);
+    int l = 0;
+    CU(launch_first_reach(S.hit, cnt, (long long)(need - before), C.d_first, C.fr_tmp, X.st, &l));
+    X.end(h);
+    X.launches += l;
+    long long out[2];
+    CU(cudaMemcpyAsync(out, C.d_first, sizeof(out), cudaMemcpyDeviceToHost, X.st));
+    CU(cudaStreamSynchronize(X.st));
+    if (out[0] > 0) {
+      *T_out = j + out[0];
+      *hits_out = need;
+      return SSA_OK;
+    }
+    before += out[1];
+    j += cnt;
+    B *= 2;
+  }
+  *hits_out = before;
+  return SSA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 parameters (Table 1; Algorithm 1 lines 1-3; Algorithm 4 lines 1-3;
+// Eq. "set_ep").  Upsilon is taken from ln(1/delta) so that the tiny
+// delta/(6 C(n,k)) inside N_max is never formed.
+// ---------------------------------------------------------------------------
+const double kOneMinusInvE = 1.0 - 1.0 / 2.718281828459045;
+
+double upsilon_ln(double eps, double ln_inv_delta) {
+  return (2.0 + 2.0 * eps / 3.0) * ln_inv_delta / (eps * eps);
+}
+
+struct Params {
+  double n_max, lambda, lambda1, lambda2, eps1, eps2, eps3;
+  int32_t i_max;
+};
+
+Params make_params(int64_t n, int k, double eps, double delta, bool dssa) {
+  Params P{};
+  const double lnC = std::lgamma((double)n + 1.0) - std::lgamma((double)k + 1.0) -
+                     std::lgamma((double)(n - k) + 1.0);
+  P.n_max = 8.0 * kOneMinusInvE / (2.0 + 2.0 * eps / 3.0) * upsilon_ln(eps, std::log(6.0 / delta) + lnC) *
+            (double)n / (double)k;
+  P.i_max = (int32_t)std::ceil(std::log2(2.0 * P.n_max / upsilon_ln(eps, std::log(3.0 / delta))));
+  if (P.i_max < 1) P.i_max = 1;
+  const double lnd = std::log(3.0 * (double)P.i_max / delta);
+  P.lambda = upsilon_ln(eps, lnd);
+  P.eps2 = eps / (2.0 * kOneMinusInvE);
+  P.eps3 = P.eps2;
+  P.eps1 = (1.0 + eps / (2.0 * (kOneMinusInvE - eps))) / (1.0 + P.eps2) - 1.0;
+  if (dssa) {
+    P.lambda1 = 1.0 + (1.0 + eps) * P.lambda;
+    P.lambda2 = 0.0;
+  } else {
+    P.lambda1 = (1.0 + P.eps1) * (1.0 + P.eps2) * upsilon_ln(P.eps3, lnd);
+    P.lambda2 = 1.0 + (1.0 + P.eps2) * upsilon_ln(P.eps2, lnd);
+  }
+  return P;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+struct ssa_solver {
+  const ssa_graph* g = nullptr;
+  int device = 0;
+  bool own_stream = false;
+  Exec X;
+  int64_t byte_cap = 0;
+};
+
+namespace {
+ssa_status check_params(const ssa_graph* g, const ssa_params* p) {
+  if (!g || !p) return fail(SSA_E_ARG, "null graph or params");
+  if (p->k < 1 || p->k > g->n) return fail(SSA_E_ARG, "k=%d outside [1, n=%lld]", p->k, (long long)g->n);
+  if (!(p->eps > 0.0 && p->eps < kOneMinusInvE)) return fail(SSA_E_ARG, "eps must lie in (0, 1-1/e)");
+  if (!(p->delta > 0.0 && p->delta < 1.0)) return fail(SSA_E_ARG, "delta must lie in (0, 1)");
+  if (p->model != SSA_IC && p->model != SSA_LT) return fail(SSA_E_ARG, "unknown model");
+  if (p->algo != SSA_ALGO_SSA && p->algo != SSA_ALGO_DSSA) return fail(SSA_E_ARG, "unknown algorithm");
+  if (p->model == SSA_LT && g->weighting != SSA_W_WC)
+    return fail(SSA_E_ARG, "LT needs weighted-cascade in-weights (SSA_W_WC)");
+  return SSA_OK;
+}
+
+ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
+  const double t0 = now_s();
+  const ssa_graph* g = sv->g;
+  TRY(check_params(g, p));
+  if (!out || !out->seeds) return fail(SSA_E_ARG, "result seeds buffer missing");
+  Exec& X = sv->X;
+  X.launches = 0;
+  X.timing = out->want_kstats != 0;
+  for (int i = 0; i < SSA_K_COUNT; ++i) out->kstats[i] = ssa_kstat{0, 0.0};
+  const bool dssa = p->algo == SSA_ALGO_DSSA;
+  const int k = p->k;
+  const int64_t n = g->n;
+  Params P = make_params(n, k, p->eps, p->delta, dssa);
+  Sampler S;
+  DevPool pool;
+  Cover C;
+  pool.byte_cap = p->pool_bytes_cap > 0 ? p->pool_bytes_cap : sv->byte_cap;
+  ssa_status st = SSA_OK;
+  std::vector<int32_t> seeds((size_t)k);
+  std::vector<int64_t> gains((size_t)k);
+  int32_t t = 0;
+  int64_t extra_rr = 0;
+  double influence = 0.0;
+  do {
+    if ((st = S.init(g, p->model, p->benefit, X)) != SSA_OK) break;
+    if ((st = C.init(n, X)) != SSA_OK) break;
+    const double scale = p->benefit ? (double)S.wsum : (double)n;
+    const int64_t base = (int64_t)std::ceil(P.lambda);
+    for (;;) {
+      t += 1;
+      const int64_t N = base << (t - 1);
+      ssa_round rec{};
+      rec.t = t;
+      rec.n_sets = N;
+      rec.check_cov = -1;
+      rec.check_T = 0;
+      rec.stat = -1.0;
+      int stop = 0;
+      if (!dssa) {
+        if ((st = S.append(pool, p->seed, 0, N - pool.count, X)) != SSA_OK) break;
+        int64_t cov = 0;
+        if ((st = C.greedy(pool, N, k, seeds.data(), gains.data(), &cov, X)) != SSA_OK) break;
+        rec.cov = cov;
+        influence = (double)cov * scale / (double)N;
+        if ((double)cov >= P.lambda1) {  // condition C1
+          const double d2 = P.eps3 * P.eps3 / (P.eps2 * P.eps2);
+          const int64_t t_max = (int64_t)std::ceil(2.0 * (double)N * (1.0 + P.eps2) / (1.0 - P.eps2) * d2);
+          const int64_t need = (int64_t)std::ceil(P.lambda2);
+          // first batch sized from the greedy's own hit rate cov/N
+          const int64_t guess = (int64_t)((double)need * (double)N / (double)cov * 1.15) + 1024;
+          int64_t T = 0, hits = 0;
+          if ((st = estimate_inf_dev(S, C, p->seed, (uint32_t)t, C.d_seeds, k, need, t_max, guess, &T, &hits, X)) !=
+              SSA_OK)
+            break;
+          extra_rr += T ? T : t_max;
+          rec.check_cov = hits;
+          rec.check_T = T;
+          if (T > 0) {
+            const double ic = scale * P.lambda2 / (double)T;
+            rec.stat = ic;
+            if ((double)cov * scale / (double)N <= (1.0 + P.eps1) * ic) stop = 1;  // condition C2
+          }
+        }
+      } else {
+        if (t == 1 && (st = S.append(pool, p->seed, 0, N, X)) != SSA_OK) break;
+        if ((st = S.append(pool, p->seed, 0, 2 * N - pool.count, X)) != SSA_OK) break;
+        int64_t cov = 0, c = 0;
+        if ((st = C.greedy(pool, N, k, seeds.data(), gains.data(), &cov, X)) != SSA_OK) break;
+        if ((st = C.coverage_range(pool, N, 2 * N, &c, X)) != SSA_OK) break;
+        rec.cov = cov;
+        rec.check_cov = c;
+        influence = (double)cov * scale / (double)N;
+        if ((double)c >= P.lambda1) {  // condition D1
+          const double ic = (double)c * scale / (double)N;
+          const double ih = (double)cov * scale / (double)N;
+          const double pw = (double)(int64_t(1) << (t - 1));
+          const double e1 = ih / ic - 1.0;
+          const double e2 = p->eps * std::sqrt(scale * (1.0 + p->eps) / (pw * ic));
+          const double e3 = p->eps * std::sqrt(scale * (1.0 + p->eps) * (kOneMinusInvE - p->eps) /
+                                               ((1.0 + p->eps / 3.0) * pw * ic));
+          const double et = (e1 + e2 + e1 * e2) * (kOneMinusInvE - p->eps) + kOneMinusInvE * e3;
+          rec.stat = et;
+          if (et <= p->eps) stop = 1;  // condition D2
+        }
+      }
+      if (!stop && ((double)N >= P.n_max || t >= P.i_max)) stop = 2;  // sample cap
+      rec.stop = stop ? 1 : 0;
+      if (out->trace && t <= out->trace_cap) out->trace[t - 1] = rec;
+      if (stop) break;
+    }
+  } while (false);
+  cudaStreamSynchronize(X.st);
+  if (st == SSA_OK) {
+    std::memcpy(out->seeds, seeds.data(), sizeof(int32_t) * (size_t)k);
+    out->influence = influence;
+    out->rounds = t;
+    out->n_rr = pool.count + extra_rr;
+    out->pool_entries = pool.entries;
+    out->edge_visits = S.edge_visits;
+    out->node_visits = S.node_visits;
+    out->cta_sets = S.cta_samples;
+    out->cta_edge_visits = S.cta_edge_visits;
+    out->cta_node_visits = S.cta_node_visits;
+    out->kernel_launches = X.launches;
+    X.collect(out->kstats);
+  } else {
+    X.collect(nullptr);
+  }
+  pool.release(X.st);
+  S.release(X.st);
+  C.release(X.st);
+  cudaStreamSynchronize(X.st);
+  out->seconds = now_s() - t0;
+  return st;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* ssa_status_str(ssa_status s) {
+  switch (s) {
+    case SSA_OK: return "ok";
+    case SSA_E_ARG: return "bad argument";
+    case SSA_E_NOMEM: return "out of memory";
+    case SSA_E_POOL_FULL: return "RR pool full";
+    case SSA_E_CUDA: return "CUDA error";
+    case SSA_E_TIMEOUT: return "device wait timed out";
+    case SSA_E_CANCELLED: return "cancelled";
+    case SSA_E_INTERNAL: return "internal error";
+    case SSA_E_NOT_READY: return "not ready";
+  }
+  return "unknown status";
+}
+
+ssa_status ssa_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    std::strncpy(buf, g_err, len - 1);
+    buf[len - 1] = 0;
+  }
+  return SSA_OK;
+}
+
+const char* ssa_version(void) { return "ssa-gb300 0.1 sm_103a"; }
+
+ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const uint32_t* thr,
+                          ssa_weighting weighting, uint64_t weight_seed, ssa_graph** out) {
+  if (!out) return fail(SSA_E_ARG, "null output handle");
+  *out = nullptr;
+  if (n < 1 || n > 0x7FFFFFFF || m < 0 || m > 0x7FFFFFFF) return fail(SSA_E_ARG, "n or m out of range");
+  if (m > 0 && (!src || !dst)) return fail(SSA_E_ARG, "null edge arrays");
+  if (weighting != SSA_W_WC && weighting != SSA_W_TRIVALENCY && weighting != SSA_W_EXPLICIT)
+    return fail(SSA_E_ARG, "unknown weighting");
+  if (weighting == SSA_W_EXPLICIT && m > 0 && !thr) return fail(SSA_E_ARG, "explicit weighting needs thr");
+  ssa_graph* g = new ssa_graph();
+  cudaGetDevice(&g->device);
+  g->n = n;
+  g->m = m;
+  g->weighting = weighting;
+  cudaStream_t st;
+  CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  int32_t *d_src = nullptr, *d_dst = nullptr;
+  uint32_t* d_thr = nullptr;
+  unsigned int* d_err = nullptr;
+  ssa_status rc = SSA_OK;
+  do {
+    const int64_t m_pad = ((m + 3) / 4) * 4 + 4;
+    if ((rc = dev_alloc(&g->off, (size_t)n + 1, st)) != SSA_OK) break;
+    if ((rc = dev_alloc(&g->edge, (size_t)m_pad, st)) != SSA_OK) break;
+    if (cudaMemsetAsync(g->edge, 0, sizeof(uint2) * (size_t)m_pad, st) != cudaSuccess) {
+      rc = fail(SSA_E_CUDA, "memset failed");
+      break;
+    }
+    g->bytes = (int64_t)(sizeof(int64_t) * (size_t)(n + 1) + sizeof(uint2) * (size_t)m_pad);
+    if ((rc = dev_alloc(&d_err, 1, st)) != SSA_OK) break;
+    cudaMemsetAsync(d_err, 0, sizeof(unsigned int), st);
+    if (m > 0) {
+      if ((rc = dev_alloc(&d_src, (size_t)m, st)) != SSA_OK) break;
+      if ((rc = dev_alloc(&d_dst, (size_t)m, st)) != SSA_OK) break;
+      cudaMemcpyAsync(d_src, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(d_dst, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, st);
+      if (weighting == SSA_W_EXPLICIT) {
+        if ((rc = dev_alloc(&d_thr, (size_t)m, st)) != SSA_OK) break;
+        cudaMemcpyAsync(d_thr, thr, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, st);
+      }
+    }
+    int launches = 0;
+    cudaError_t e = build_graph(n, m, d_src, d_dst, d_thr, weighting, weight_seed, g->off, g->edge, d_err, st,
+                                &launches);
+    if (e != cudaSuccess) {
+      rc = fail(e == cudaErrorMemoryAllocation ? SSA_E_NOMEM : SSA_E_CUDA, "graph build: %s", cudaGetErrorString(e));
+      break;
+    }
+    unsigned int herr = 0;
+    cudaMemcpyAsync(&herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = fail(SSA_E_CUDA, "graph build: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (herr) rc = fail(SSA_E_ARG, "edge endpoint outside [0, n)");
+  } while (false);
+  if (d_src) cudaFreeAsync(d_src, st);
+  if (d_dst) cudaFreeAsync(d_dst, st);
+  if (d_thr) cudaFreeAsync(d_thr, st);
+  if (d_err) cudaFreeAsync(d_err, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (rc != SSA_OK) {
+    if (g->off) cudaFree(g->off);
+    if (g->edge) cudaFree(g->edge);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return SSA_OK;
+}
+
+ssa_status ssa_free_graph(ssa_graph* g) {
+  if (!g) return SSA_OK;
+  cudaDeviceSynchronize();
+  if (g->off) cudaFree(g->off);
+  if (g->edge) cudaFree(g->edge);
+  delete g;
+  return SSA_OK;
+}
+
+ssa_status ssa_graph_info(const ssa_graph* g, int64_t* n, int64_t* m, int64_t* bytes) {
+  if (!g) return fail(SSA_E_ARG, "null graph");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (bytes) *bytes = g->bytes;
+  return SSA_OK;
+}
+
+ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint32_t* thr) {
+  if (!g) return fail(SSA_E_ARG, "null graph");
+  if (off) CU(cudaMemcpy(off, g->off, sizeof(int64_t) * (size_t)(g->n + 1), cudaMemcpyDeviceToHost));
+  if ((src || thr) && g->m > 0) {
+    std::vector<uint2> e((size_t)g->m);
+    CU(cudaMemcpy(e.data(), g->edge, sizeof(uint2) * (size_t)g->m, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < g->m; ++i) {
+      if (src) src[i] = (int32_t)e[(size_t)i].x;
+      if (thr) thr[i] = e[(size_t)i].y;
+    }
+  }
+  return SSA_OK;
+}
+
+ssa_status ssa_solver_create(const ssa_graph* g, void* stream, int64_t pool_bytes_cap, ssa_solver** out) {
+  if (!g || !out) return fail(SSA_E_ARG, "null graph or output");
+  ssa_solver* s = new ssa_solver();
+  s->g = g;
+  cudaGetDevice(&s->device);
+  if (stream) {
+    s->X.st = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->X.st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(SSA_E_CUDA, "stream create: %s", cudaGetErrorString(e));
+    }
+    s->own_stream = true;
+  }
+  if (pool_bytes_cap <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    pool_bytes_cap = (int64_t)((double)fr * 0.6);
+  }
+  s->byte_cap = pool_bytes_cap;
+  *out = s;
+  return SSA_OK;
+}
+
+ssa_status ssa_solver_solve(ssa_solver* s, const ssa_params* p, ssa_result* out) {
+  if (!s) return fail(SSA_E_ARG, "null solver");
+  return solve_impl(s, p, out);
+}
+
+ssa_status ssa_solver_free(ssa_solver* s) {
+  if (!s) return SSA_OK;
+  cudaStreamSynchronize(s->X.st);
+  if (s->own_stream) cudaStreamDestroy(s->X.st);
+  s->X.st = nullptr;
+  delete s;
+  return SSA_OK;
+}
+
+ssa_status ssa_solve(const ssa_graph* g, const ssa_params* p, ssa_result* out) {
+  ssa_solver* s = nullptr;
+  TRY(ssa_solver_create(g, nullptr, p ? p->pool_bytes_cap : 0, &s));
+  ssa_status st = ssa_solver_solve(s, p, out);
+  ssa_solver_free(s);
+  return st;
+}
+
+// ---- pools (hot-path steps one by one) ----
+struct ssa_pool {
+  const ssa_graph* g = nullptr;
+  int device = 0;
+  uint64_t seed = 0;
+  uint32_t stream = 0;
+  Exec X;
+  Sampler S;
+  DevPool P;
+  Cover C;
+};
+
+ssa_status ssa_pool_create(const ssa_graph* g, ssa_model model, uint64_t seed, uint32_t stream,
+                           const uint32_t* benefit, ssa_pool** out) {
+  if (!g || !out) return fail(SSA_E_ARG, "null graph or output");
+  if (model != SSA_IC && model != SSA_LT) return fail(SSA_E_ARG, "unknown model");
+  if (model == SSA_LT && g->weighting != SSA_W_WC) return fail(SSA_E_ARG, "LT needs SSA_W_WC");
+  if (stream > 255) return fail(SSA_E_ARG, "stream must be < 256");
+  ssa_pool* p = new ssa_pool();
+  p->g = g;
+  p->seed = seed;
+  p->stream = stream;
+  cudaGetDevice(&p->device);
+  if (cudaStreamCreateWithFlags(&p->X.st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete p;
+    return fail(SSA_E_CUDA, "stream create failed");
+  }
+  ssa_status st = p->S.init(g, model, benefit, p->X);
+  if (st == SSA_OK) st = p->C.init(g->n, p->X);
+  if (st != SSA_OK) {
+    ssa_pool_free(p);
+    return st;
+  }
+  *out = p;
+  return SSA_OK;
+}
+
+ssa_status ssa_pool_free(ssa_pool* p) {
+  if (!p) return SSA_OK;
+  p->P.release(p->X.st);
+  p->S.release(p->X.st);
+  p->C.release(p->X.st);
+  cudaStreamSynchronize(p->X.st);
+  cudaStreamDestroy(p->X.st);
+  delete p;
+  return SSA_OK;
+}
+
+ssa_status ssa_pool_grow(ssa_pool* p, int64_t count) {
+  if (!p) return fail(SSA_E_ARG, "null pool");
+  if (count <= p->P.count) return SSA_OK;
+  return p->S.append(p->P, p->seed, p->stream, count - p->P.count, p->X);
+}
+
+ssa_status ssa_pool_info(const ssa_pool* p, int64_t* count, int64_t* entries, int64_t* edge_visits) {
+  if (!p) return fail(SSA_E_ARG, "null pool");
+  if (count) *count = p->P.count;
+  if (entries) *entries = p->P.entries;
+  if (edge_visits) *edge_visits = p->S.edge_visits;
+  return SSA_OK;
+}
+
+ssa_status ssa_pool_export(const ssa_pool* pc, int64_t first, int64_t count, int64_t* off, int32_t* nodes,
+                           int64_t cap) {
+  ssa_pool* p = const_cast<ssa_pool*>(pc);
+  if (!p || !off) return fail(SSA_E_ARG, "null pool or offsets");
+  if (first < 0 || count < 0 || first + count > p->P.count) return fail(SSA_E_ARG, "set range outside the pool");
+  std::vector<int32_t> len((size_t)count);
+  if (count > 0)
+    CU(cudaMemcpy(len.data(), p->P.set_len + first, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost));
+  off[0] = 0;
+  for (int64_t i = 0; i < count; ++i) off[i + 1] = off[i] + len[(size_t)i];
+  if (off[count] > cap || (!nodes && off[count] > 0)) return fail(SSA_E_ARG, "nodes buffer too small");
+  if (off[count] == 0) return SSA_OK;
+  int64_t* d_off = nullptr;
+  int32_t* d_out = nullptr;
+  TRY(dev_alloc(&d_off, (size_t)count + 1, p->X.st));
+  TRY(dev_alloc(&d_out, (size_t)off[count], p->X.st));
+  CU(cudaMemcpyAsync(d_off, off, sizeof(int64_t) * (size_t)(count + 1), cudaMemcpyHostToDevice, p->X.st));
+  CU(launch_gather_sets(p->P.nodes, p->P.set_start, p->P.set_len, d_off, first, count, d_out, p->X.st));
+  CU(cudaMemcpyAsync(nodes, d_out, sizeof(int32_t) * (size_t)off[count], cudaMemcpyDeviceToHost, p->X.st));
+  CU(cudaStreamSynchronize(p->X.st));
+  dev_free(d_off, p->X.st);
+  dev_free(d_out, p->X.st);
+  CU(cudaStreamSynchronize(p->X.st));
+  return SSA_OK;
+}
+
+ssa_status ssa_pool_counts(ssa_pool* p, int64_t N, int32_t* cnt) {
+  if (!p || !cnt) return fail(SSA_E_ARG, "null pool or output");
+  if (N < 0 || N > p->P.count) return fail(SSA_E_ARG, "N outside the pool");
+  TRY(p->C.build_index(p->P, N, p->X));
+  CU(cudaMemcpyAsync(cnt, p->C.cnt, sizeof(int32_t) * (size_t)p->g->n, cudaMemcpyDeviceToHost, p->X.st));
+  CU(cudaStreamSynchronize(p->X.st));
+  return SSA_OK;
+}
+
+ssa_status ssa_max_coverage(ssa_pool* p, int64_t N, int32_t k, int32_t* seeds, int64_t* gains, int64_t* cov) {
+  if (!p || !seeds || !gains || !cov) return fail(SSA_E_ARG, "null argument");
+  if (N < 0 || N > p->P.count) return fail(SSA_E_ARG, "N outside the pool");
+  if (k < 1 || k > p->g->n) return fail(SSA_E_ARG, "k outside [1, n]");
+  return p->C.greedy(p->P, N, k, seeds, gains, cov, p->X);
+}
+
+ssa_status ssa_coverage(ssa_pool* p, int64_t first, int64_t count, const int32_t* seeds, int32_t k, int64_t* cov) {
+  if (!p || !cov || (k > 0 && !seeds)) return fail(SSA_E_ARG, "null argument");
+  if (first < 0 || count < 0 || first + count > p->P.count) return fail(SSA_E_ARG, "set range outside the pool");
+  for (int i = 0; i < k; ++i)
+    if (seeds[i] < 0 || seeds[i] >= p->g->n) return fail(SSA_E_ARG, "seed id outside [0, n)");
+  int32_t* d = nullptr;
+  TRY(dev_alloc(&d, (size_t)std::max(k, 1), p->X.st));
+  if (k > 0) CU(cudaMemcpyAsync(d, seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, p->X.st));
+  CU(cudaMemsetAsync(p->C.in_seed, 0, (size_t)p->C.n_pad, p->X.st));
+  if (k > 0) CU(launch_set_bits(d, k, nullptr, p->C.in_seed, p->X.st));
+  ssa_status st = p->C.coverage_range(p->P, first, first + count, cov, p->X);
+  dev_free(d, p->X.st);
+  cudaStreamSynchronize(p->X.st);
+  return st;
+}
+
+ssa_status ssa_estimate_inf(const ssa_graph* g, ssa_model model, uint64_t seed, uint32_t stream,
+                            const uint32_t* benefit, const int32_t* seeds, int32_t k, double lambda2, int64_t t_max,
+                            int64_t* T, int64_t* hits) {
+  if (!g || !T || !hits || (k > 0 && !seeds)) return fail(SSA_E_ARG, "null argument");
+  if (stream > 255) return fail(SSA_E_ARG, "stream must be < 256");
+  if (!(lambda2 >= 1.0) || t_max < 0) return fail(SSA_E_ARG, "need lambda2 >= 1 and t_max >= 0");
+  for (int i = 0; i < k; ++i)
+    if (seeds[i] < 0 || seeds[i] >= g->n) return fail(SSA_E_ARG, "seed id outside [0, n)");
+  ssa_pool* p = nullptr;
+  TRY(ssa_pool_create(g, model, seed, stream, benefit, &p));
+  ssa_status st = SSA_OK;
+  int32_t* d = nullptr;
+  do {
+    if ((st = dev_alloc(&d, (size_t)std::max(k, 1), p->X.st)) != SSA_OK) break;
+    if (k > 0 && cudaMemcpyAsync(d, seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, p->X.st) !=
+                     cudaSuccess) {
+      st = fail(SSA_E_CUDA, "copy seeds");
+      break;
+    }
+    const int64_t need = (int64_t)std::ceil(lambda2);
+    st = estimate_inf_dev(p->S, p->C, seed, stream, d, k, need, t_max, std::min<int64_t>(t_max, 1 << 16), T, hits,
+                          p->X);
+  } while (false);
+  dev_free(d, p->X.st);
+  ssa_pool_free(p);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Graph store (Sec. 2): in-edge CSR with uint32 live thresholds, built on
+// the device.  Edges are ordered by (dst, src, input position) with a stable
+// device radix sort (CUB, header source from the CUDA toolkit); offsets come
+// from segment boundaries of the sorted keys, thresholds from the weighting
+// rule: weighted cascade w = 1/d_in(v) (Sec. 6.1), trivalency, or explicit.
+#include <cub/device/device_radix_sort.cuh>
+
+#include "device.cuh"
+
+namespace ssa {
+
+namespace {
+
+__global__ void k_make_keys(const int32_t* src, const int32_t* dst, int64_t n, int64_t m, int bits,
+                            unsigned long long* keys, int32_t* vals, unsigned int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = src[i], d = dst[i];
+    if (s < 0 || s >= n || d < 0 || d >= n) {
+      atomicExch(err, 1u);
+      keys[i] = 0;
+    } else {
+      keys[i] = ((unsigned long long)d << bits) | (unsigned long long)s;
+    }
+    vals[i] = (int32_t)i;
+  }
+}
+
+// off[v] = first sorted position whose dst >= v.
+__global__ void k_offsets(const unsigned long long* keys, int64_t n, int64_t m, int bits, int64_t* off) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = (e == 0) ? -1 : (int64_t)(keys[e - 1] >> bits);
+    const int64_t cur = (e == m) ? n : (int64_t)(keys[e] >> bits);
+    for (int64_t v = prev + 1; v <= cur; ++v) off[v] = e;
+  }
+}
+
+__global__ void k_fill_edges(const unsigned long long* keys, const int32_t* vals, const int64_t* off, int64_t m,
+                             int bits, int weighting, uint64_t weight_seed, const uint32_t* thr_in, uint2* edge) {
+  const unsigned long long mask = (1ull << bits) - 1ull;
+  const uint32_t TRI[3] = {429496729u, 42949672u, 4294967u};  // floor(2^32 p), p = 0.1, 0.01, 0.001
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = keys[e];
+    const uint32_t s = (uint32_t)(k & mask);
+    uint32_t t;
+    if (weighting == 0) {
+      const int64_t v = (int64_t)(k >> bits);
+      const uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+      t = (d == 1) ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / d);
+    } else if (weighting == 1) {
+      const uint4 r = keyed_draw(weight_seed, PURPOSE_WEIGHT, 0, 0, (uint64_t)e);
+      t = TRI[__umulhi(r.x, 3u)];
+    } else {
+      t = thr_in[vals[e]];
+    }
+    edge[e] = make_uint2(s, t);
+  }
+}
+
+int grid_for(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const uint32_t* d_thr_in,
+                        int weighting, uint64_t weight_seed, int64_t* d_off, uint2* d_edge, unsigned int* d_err,
+                        cudaStream_t st, int* launches) {
+  int bits = 1;
+  while ((1ll << bits) < n) ++bits;
+  cudaError_t e = cudaSuccess;
+  if (m == 0) {
+    e = cudaMemsetAsync(d_off, 0, sizeof(int64_t) * (size_t)(n + 1), st);
+    return e;
+  }
+  unsigned long long *k_in = nullptr, *k_out = nullptr;
+  int32_t *v_in = nullptr, *v_out = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  do {
+    if ((e = cudaMallocAsync(&k_in, sizeof(unsigned long long) * (size_t)m, st)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&k_out, sizeof(unsigned long long) * (size_t)m, st)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&v_in, sizeof(int32_t) * (size_t)m, st)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&v_out, sizeof(int32_t) * (size_t)m, st)) != cudaSuccess) break;
+    k_make_keys<<<grid_for(m, 256), 256, 0, st>>>(d_src, d_dst, n, m, bits, k_in, v_in, d_err);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k_in, k_out, v_in, v_out, (int64_t)m, 0, 2 * bits,
+                                             st)) != cudaSuccess)
+      break;
+    if ((e = cudaMallocAsync(&tmp, tmp_bytes, st)) != cudaSuccess) break;
+    if ((e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, v_in, v_out, (int64_t)m, 0, 2 * bits,
+                                             st)) != cudaSuccess)
+      break;
+    *launches += 2 * ((2 * bits + 7) / 8) + 1;
+    k_offsets<<<grid_for(m + 1, 256), 256, 0, st>>>(k_out, n, m, bits, d_off);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    k_fill_edges<<<grid_for(m, 256), 256, 0, st>>>(k_out, v_out, d_off, m, bits, weighting, weight_seed, d_thr_in,
+                                                   d_edge);
+    ++*launches;
+    e = cudaGetLastError();
+  } while (false);
+  if (k_in) cudaFreeAsync(k_in, st);
+  if (k_out) cudaFreeAsync(k_out, st);
+  if (v_in) cudaFreeAsync(v_in, st);
+  if (v_out) cudaFreeAsync(v_out, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  return e;
+}
+
+}  // namespace ssa

@@ -1,0 +1,128 @@
+// Internal interface between the host driver (api.cpp) and the sm_103a
+// kernels (*.cu).  Plain structs of device pointers; no torch types.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ssa {
+
+// Device-resident in-edge CSR (Sec. 2).  Edge records interleave the tail
+// node and the uint32 live threshold so one 8-byte load serves an edge and a
+// 4-edge group (the unit of one Philox draw) is one aligned 32-byte sector.
+struct GraphView {
+  int64_t n = 0, m = 0;
+  const int64_t* off = nullptr;  // n+1
+  const uint2* edge = nullptr;   // m rounded up to a multiple of 4 (+4): {src, thr}
+};
+
+// Device counters of one sampling batch.
+struct Counters {
+  unsigned long long work;         // warp tier: next sample index
+  unsigned long long big_count;    // samples handed to the CTA tier
+  unsigned long long big_work;     // CTA tier: next list index
+  unsigned long long cursor;       // pool entries reserved (absolute)
+  unsigned long long edge_visits;  // in-edges examined
+  unsigned long long node_visits;  // nodes added to RR sets
+  unsigned long long cta_edge_visits;  // the CTA tier's share of the two above
+  unsigned long long cta_node_visits;
+  unsigned int pool_overflow;      // a reservation passed pool_cap
+  unsigned int error;              // internal error flag
+};
+
+enum : int { MODE_STORE = 0, MODE_HIT = 1 };
+
+struct SampleJob {
+  GraphView g;
+  int model = 0;                 // 0 IC, 1 LT
+  uint64_t seed = 0;
+  uint32_t stream = 0;
+  int64_t j0 = 0, count = 0;     // samples [j0, j0+count)
+  const uint64_t* bprefix = nullptr;  // WRIS prefix sums (n+1) or null
+  int mode = MODE_STORE;
+  // MODE_STORE: flat pool entries + per-sample extents
+  int32_t* pool_nodes = nullptr;
+  int32_t* pool_samp = nullptr;
+  int64_t pool_cap = 0;
+  int64_t* set_start = nullptr;  // indexed by absolute sample id
+  int32_t* set_len = nullptr;
+  // MODE_HIT: seed membership bits, per-sample flag (index j - j0)
+  const uint32_t* seed_bits = nullptr;
+  uint8_t* hit = nullptr;
+  // CTA tier hand-off and scratch
+  int64_t* big_list = nullptr;   // capacity `count`
+  uint32_t* slot_bitmap = nullptr;  // per CTA slot: bitmap_words (unused when the bitmap is in smem)
+  int32_t* slot_queue = nullptr;    // per CTA slot: n entries
+  int64_t bitmap_words = 0;
+  Counters* ctr = nullptr;
+};
+
+struct LaunchCfg {
+  int num_sms = 152;
+  int warp_blocks = 0;   // grid of the warp tier
+  int cta_blocks = 0;    // grid of the CTA tier (= number of scratch slots)
+  int cta_threads = 1024;
+  bool cta_smem_bitmap = false;
+  int64_t smem_bitmap_bytes = 0;
+};
+
+// ---- graph build -------------------------------------------------------
+// Sorts edges by (dst, src, input position), builds off/edge records and
+// thresholds.  d_src/d_dst/d_thr_in are device arrays of length m.
+cudaError_t build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst,
+                        const uint32_t* d_thr_in, int weighting, uint64_t weight_seed,
+                        int64_t* d_off, uint2* d_edge, unsigned int* d_err, cudaStream_t st,
+                        int* launches);
+
+// ---- sampling -----------------------------------------------------------
+LaunchCfg sampler_config(const GraphView& g, int model);
+size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c);
+cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st);
+cudaError_t launch_sample_cta(const SampleJob& J, const LaunchCfg& c, cudaStream_t st);
+
+// ---- index, greedy, stare -----------------------------------------------
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+// entries [e0, e1); with samp non-null only samples in [jlo, jhi) count
+cudaError_t launch_count_nodes(const int32_t* nodes, const int32_t* samp, int64_t e0, int64_t e1, int64_t jlo,
+                               int64_t jhi, int32_t* cnt, cudaStream_t st, int num_sms);
+// exclusive scan of int32 counts into int64 offsets (n+1 outputs); tmp >= scan_tmp_bytes(n)
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t launch_exclusive_scan(const int32_t* in, int64_t n, int64_t* out, void* tmp, cudaStream_t st,
+                                  int* launches);
+cudaError_t launch_scatter_index(const int32_t* nodes, const int32_t* samp, int64_t e0, int64_t e1, int64_t jlo,
+                                 int64_t jhi, unsigned long long* cur, int32_t* inv_samp, cudaStream_t st,
+                                 int num_sms);
+
+struct GreedyBufs {
+  int32_t* cnt;                 // n, working marginal gains
+  const int64_t* inv_off;       // n+1
+  const int32_t* inv_samp;      // entries
+  const int32_t* pool_nodes;
+  const int64_t* set_start;
+  const int32_t* set_len;
+  uint8_t* covered;             // N
+  uint8_t* in_seed;             // n
+  unsigned long long* partial;  // argmax partials
+  int32_t* seeds;               // k (device)
+  int32_t* gains;               // k (device)
+  int64_t n;
+  int argmax_blocks;
+};
+cudaError_t launch_greedy_step(const GreedyBufs& b, int step, cudaStream_t st, int num_sms);
+
+cudaError_t launch_mark_hits(const int32_t* nodes, const int32_t* samp, int64_t e0, int64_t e1,
+                             const uint8_t* in_seed, int64_t j0, int64_t j1, uint8_t* hit, cudaStream_t st,
+                             int num_sms);
+cudaError_t launch_count_flags(const uint8_t* flags, int64_t count, unsigned long long* out,
+                               cudaStream_t st, int num_sms);
+// First T (1-based) in flags[0, count) where base + prefix hits reaches `need`;
+// out[0] = T or 0, out[1] = hits in [0, count).
+cudaError_t launch_first_reach(const uint8_t* flags, int64_t count, long long need_minus_base,
+                               long long* out, void* tmp, cudaStream_t st, int* launches);
+size_t first_reach_tmp_bytes(int64_t count);
+
+cudaError_t launch_set_bits(const int32_t* ids, int k, uint32_t* bits, uint8_t* bytes, cudaStream_t st);
+cudaError_t launch_gather_sets(const int32_t* pool_nodes, const int64_t* set_start, const int32_t* set_len,
+                               const int64_t* out_off, int64_t first, int64_t count, int32_t* out,
+                               cudaStream_t st);
+
+}  // namespace ssa

@@ -1,0 +1,455 @@
+// RR-set samplers (Definition 2) for IC and LT (Sec. 2.1) on sm_103a.
+//
+// Two tiers share one work list of sample ids:
+//   * warp tier: one warp per sample, visited set as an open-addressing hash
+//     in shared memory and the BFS queue beside it.  Sets that outgrow the
+//     queue are handed to the CTA tier (their partial work is dropped).
+//   * CTA tier: one CTA per sample, visited set as an n-bit bitmap (shared
+//     memory when it fits, else a per-CTA global slot), level-synchronous
+//     BFS with warps pulling 32-node batches from the current level.
+// IC frontier expansion is edge-balanced inside a warp: 32 frontier nodes'
+// in-edge ranges are cut into 4-edge groups (the unit of one Philox draw, one
+// aligned 32-byte sector of {src,thr} records) and the groups are dealt to
+// lanes by a warp prefix sum.
+#include "device.cuh"
+
+namespace ssa {
+
+namespace {
+
+constexpr int WT_WARPS = 8;      // warps per warp-tier block
+constexpr int WT_HASH = 1024;    // hash slots per warp (power of two)
+constexpr int WT_QCAP = 512;     // largest IC set kept in the warp tier
+constexpr int LT_QCAP = 1024;    // largest LT walk kept in the warp tier
+
+__device__ __forceinline__ int32_t pick_root(const SampleJob& J, int64_t j) {
+  const uint4 r = keyed_draw(J.seed, PURPOSE_ROOT, J.stream, j, 0);
+  const int64_t n = J.g.n;
+  if (!J.bprefix) return (int32_t)__umulhi(r.x, (uint32_t)n);
+  // WRIS (Sec. 6.3.1): the node whose benefit interval holds a 64-bit target
+  const uint64_t W = J.bprefix[n];
+  const uint64_t r64 = (uint64_t)r.x | ((uint64_t)r.y << 32);
+  const uint64_t target = __umul64hi(r64, W);
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (J.bprefix[mid + 1] > target) hi = mid; else lo = mid + 1;
+  }
+  return (int32_t)lo;
+}
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t u) { return (u * 0x9E3779B1u) >> 22; }  // 10 bits
+
+// Insert u into the warp's hash set; true when u was not there.
+__device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u) {
+  const uint32_t key = u + 1u;
+  uint32_t h = hash_slot(u);
+  for (int probe = 0; probe < WT_HASH; ++probe) {
+    const uint32_t prev = atomicCAS(H + h, 0u, key);
+    if (prev == 0u) return true;
+    if (prev == key) return false;
+    h = (h + 1u) & (WT_HASH - 1);
+  }
+  return false;  // not reached: the table is never more than 5/8 full
+}
+
+// Edge-balanced expansion of up to 32 frontier nodes (lane i holds node v or
+// -1).  For each live in-edge the lane holding it gets visit(u, true); every
+// lane calls visit 4 times per 32-group slab (uniform control flow), and the
+// expansion stops early when visit returns true (must be warp-uniform).
+template <class Visit>
+__device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, uint2 key, uint32_t jlo, uint32_t cw,
+                                          int lane, unsigned long long& ev, Visit&& visit) {
+  int64_t lo = 0, hi = 0;
+  if (v >= 0) {
+    lo = __ldg(g.off + v);
+    hi = __ldg(g.off + v + 1);
+  }
+  ev += (unsigned long long)(hi - lo);
+  const int ng = (hi > lo) ? (int)(((hi + 3) >> 2) - (lo >> 2)) : 0;
+  const int incl = warp_inclusive_scan(ng, lane);
+  const int excl = incl - ng;
+  const int total = __shfl_sync(FULL_MASK, incl, 31);
+  for (int base = 0; base < total; base += 32) {
+    const int q = base + lane;
+    int owner = 0;
+#pragma unroll
+    for (int s = 16; s; s >>= 1) {
+      const int t = __shfl_sync(FULL_MASK, incl, owner + s - 1);
+      if (t <= q) owner += s;
+    }
+    owner = owner > 31 ? 31 : owner;
+    const int64_t olo = __shfl_sync(FULL_MASK, lo, owner);
+    const int64_t ohi = __shfl_sync(FULL_MASK, hi, owner);
+    const int oex = __shfl_sync(FULL_MASK, excl, owner);
+    uint32_t c0 = NO_NODE, c1 = NO_NODE, c2 = NO_NODE, c3 = NO_NODE;
+    if (q < total) {
+      const int64_t grp = (olo >> 2) + (q - oex);
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)(grp >> 32), jlo, cw), key);
+      const uint4* p = reinterpret_cast<const uint4*>(g.edge) + grp * 2;
+      const uint4 a = __ldg(p), b = __ldg(p + 1);
+      const int64_t e = grp * 4;
+      if (e >= olo && e < ohi && edge_live(r.x, a.y)) c0 = a.x;
+      if (e + 1 >= olo && e + 1 < ohi && edge_live(r.y, a.w)) c1 = a.z;
+      if (e + 2 >= olo && e + 2 < ohi && edge_live(r.z, b.y)) c2 = b.x;
+      if (e + 3 >= olo && e + 3 < ohi && edge_live(r.w, b.w)) c3 = b.z;
+    }
+    if (visit(c0)) return true;
+    if (visit(c1)) return true;
+    if (visit(c2)) return true;
+    if (visit(c3)) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev, unsigned long long nv, int lane,
+                                            bool cta_tier) {
+  ev = warp_sum(ev);
+  nv = warp_sum(nv);
+  if (lane == 0) {
+    if (ev) atomicAdd(&ctr->edge_visits, ev);
+    if (nv) atomicAdd(&ctr->node_visits, nv);
+    if (cta_tier && ev) atomicAdd(&ctr->cta_edge_visits, ev);
+    if (cta_tier && nv) atomicAdd(&ctr->cta_node_visits, nv);
+  }
+}
+
+// Store a finished set of `size` nodes held in Q (shared or global) for the
+// warp starting at lane 0.. ; returns nothing, flags pool overflow.
+template <typename QT>
+__device__ __forceinline__ void warp_store_set(const SampleJob& J, int64_t j, const QT* Q, int size, int lane) {
+  unsigned long long pos = 0;
+  if (lane == 0) pos = atomicAdd(&J.ctr->cursor, (unsigned long long)size);
+  pos = __shfl_sync(FULL_MASK, pos, 0);
+  if (pos + (unsigned long long)size <= (unsigned long long)J.pool_cap) {
+    for (int i = lane; i < size; i += 32) {
+      J.pool_nodes[pos + i] = Q[i];
+      J.pool_samp[pos + i] = (int32_t)j;
+    }
+    if (lane == 0) {
+      J.set_start[j] = (int64_t)pos;
+      J.set_len[j] = size;
+    }
+  } else if (lane == 0) {
+    atomicExch(&J.ctr->pool_overflow, 1u);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
+  __shared__ __align__(16) uint32_t s_hash[WT_WARPS][WT_HASH];
+  __shared__ int32_t s_q[WT_WARPS][WT_QCAP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* H = s_hash[wid];
+  int32_t* Q = s_q[wid];
+  uint4* H4 = reinterpret_cast<uint4*>(H);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
+  __syncwarp();
+  const uint2 key = philox_key(J.seed);
+  unsigned long long ev = 0, nv = 0;
+  for (;;) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
+    idx = __shfl_sync(FULL_MASK, idx, 0);
+    if (idx >= (unsigned long long)J.count) break;
+    const int64_t j = J.j0 + (int64_t)idx;
+    const uint32_t cw = ctr_word3(PURPOSE_IC, J.stream, j);
+    const int32_t root = pick_root(J, j);
+    if (lane == 0) {
+      H[hash_slot((uint32_t)root)] = (uint32_t)root + 1u;
+      Q[0] = root;
+    }
+    int tail = 1, head = 0;
+    bool overflow = false;
+    bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
+    __syncwarp();
+    auto visit = [&](uint32_t u) -> bool {
+      const bool is_new = (u != NO_NODE) && hash_insert(H, u);
+      const unsigned m = __ballot_sync(FULL_MASK, is_new);
+      bool h = false;
+      if (is_new) {
+        const int pos = tail + __popc(m & lt_mask);
+        if (pos < WT_QCAP) Q[pos] = (int32_t)u;
+        if (MODE == MODE_HIT) h = test_bit(J.seed_bits, u);
+      }
+      tail += __popc(m);
+      if (MODE == MODE_HIT) hit = __any_sync(FULL_MASK, h) || hit;
+      if (tail > WT_QCAP) overflow = true;
+      return overflow || hit;
+    };
+    while (head < tail && !overflow && !hit) {
+      const int cnt = min(32, tail - head);
+      __syncwarp();
+      const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
+      __syncwarp();
+      expand_ic(J.g, v, key, (uint32_t)j, cw, lane, ev, visit);
+      head += cnt;
+    }
+    __syncwarp();
+    if (overflow) {
+      if (lane == 0) {
+        const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
+        J.big_list[b] = j;
+      }
+    } else {
+      if (MODE == MODE_STORE) warp_store_set(J, j, Q, tail, lane);
+      else if (lane == 0) J.hit[idx] = hit ? 1 : 0;
+      if (lane == 0) nv += (unsigned long long)tail;
+    }
+    __syncwarp();
+    for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+  }
+  flush_stats(J.ctr, ev, nv, lane, false);
+}
+
+// LT live-edge walk (one keyed in-neighbour per node), warp per sample: every
+// lane follows the same walk; membership of the next node is checked by the
+// 32 lanes over the walk list in shared memory.
+template <int MODE>
+__global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
+  __shared__ int32_t s_q[WT_WARPS][LT_QCAP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* Q = s_q[wid];
+  const uint2 key = philox_key(J.seed);
+  unsigned long long ev = 0, nv = 0;
+  for (;;) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
+    idx = __shfl_sync(FULL_MASK, idx, 0);
+    if (idx >= (unsigned long long)J.count) break;
+    const int64_t j = J.j0 + (int64_t)idx;
+    const uint32_t cw = ctr_word3(PURPOSE_LT, J.stream, j);
+    const int32_t root = pick_root(J, j);
+    if (lane == 0) Q[0] = root;
+    int tail = 1;
+    bool overflow = false;
+    bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
+    int32_t cur = root;
+    __syncwarp();
+    while (!hit) {
+      const int64_t lo = __ldg(J.g.off + cur), hi = __ldg(J.g.off + cur + 1);
+      const int64_t d = hi - lo;
+      if (d == 0) break;
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)cur, 0u, (uint32_t)j, cw), key);
+      const int32_t u = (int32_t)__ldg(&J.g.edge[lo + __umulhi(r.x, (uint32_t)d)].x);
+      if (lane == 0) ev += 1;
+      bool found = false;
+      for (int i = lane; i < tail; i += 32) found |= (Q[i] == u);
+      if (__any_sync(FULL_MASK, found)) break;
+      if (tail >= LT_QCAP) {
+        overflow = true;
+        break;
+      }
+      if (lane == 0) Q[tail] = u;
+      ++tail;
+      __syncwarp();
+      if (MODE == MODE_HIT) hit = test_bit(J.seed_bits, (uint32_t)u);
+      cur = u;
+    }
+    __syncwarp();
+    if (overflow) {
+      if (lane == 0) {
+        const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
+        J.big_list[b] = j;
+      }
+    } else {
+      if (MODE == MODE_STORE) warp_store_set(J, j, Q, tail, lane);
+      else if (lane == 0) J.hit[idx] = hit ? 1 : 0;
+      if (lane == 0) nv += (unsigned long long)tail;
+    }
+    __syncwarp();
+  }
+  flush_stats(J.ctr, ev, nv, lane, false);
+}
+
+// CTA tier: one CTA per large sample.
+template <int MODE, bool SMEM_BITMAP>
+__global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
+  extern __shared__ __align__(16) uint32_t s_bits[];
+  __shared__ long long s_item;
+  __shared__ int s_tail, s_next, s_hit;
+  __shared__ unsigned long long s_pos;
+  const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t n = J.g.n;
+  uint32_t* bits = SMEM_BITMAP ? s_bits : J.slot_bitmap + (size_t)blockIdx.x * (size_t)J.bitmap_words;
+  int32_t* Q = J.slot_queue + (size_t)blockIdx.x * (size_t)n;
+  if (SMEM_BITMAP)
+    for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
+  const uint2 key = philox_key(J.seed);
+  const long long big_count = (long long)*((volatile unsigned long long*)&J.ctr->big_count);
+  unsigned long long ev = 0, nv = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_item = (long long)atomicAdd(&J.ctr->big_work, 1ull);
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= big_count) break;
+    const int64_t j = J.big_list[item];
+    const int32_t root = pick_root(J, j);
+    if (tid == 0) {
+      bits[root >> 5] |= 1u << (root & 31);
+      Q[0] = root;
+      s_tail = 1;
+      s_hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
+    }
+    __syncthreads();
+    if (J.model == 0) {
+      const uint32_t cw = ctr_word3(PURPOSE_IC, J.stream, j);
+      int lvl_begin = 0, lvl_end = 1;
+      for (;;) {
+        // every thread is past the previous barrier and nobody writes s_hit
+        // until the next one, so this exit test is uniform across the CTA
+        if (lvl_begin >= lvl_end || s_hit) break;
+        if (tid == 0) s_next = lvl_begin;
+        __syncthreads();
+        for (;;) {
+          int b = 0;
+          if (lane == 0) b = atomicAdd(&s_next, 32);
+          b = __shfl_sync(FULL_MASK, b, 0);
+          if (b >= lvl_end) break;
+          const int cnt = min(32, lvl_end - b);
+          const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
+          auto visit = [&](uint32_t u) -> bool {
+            bool is_new = false;
+            if (u != NO_NODE) {
+              const uint32_t mask = 1u << (u & 31);
+              is_new = !(atomicOr(bits + (u >> 5), mask) & mask);
+            }
+            const unsigned m = __ballot_sync(FULL_MASK, is_new);
+            if (m) {
+              int base = 0;
+              if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
+              base = __shfl_sync(FULL_MASK, base, 0);
+              if (is_new) {
+                Q[base + __popc(m & lt_mask)] = (int32_t)u;
+                if (MODE == MODE_HIT && test_bit(J.seed_bits, u)) s_hit = 1;
+              }
+            }
+            if (MODE == MODE_HIT) return __any_sync(FULL_MASK, *(volatile int*)&s_hit != 0);
+            return false;
+          };
+          if (expand_ic(J.g, v, key, (uint32_t)j, cw, lane, ev, visit)) break;
+        }
+        __syncthreads();
+        lvl_begin = lvl_end;
+        lvl_end = s_tail;
+        __syncthreads();
+      }
+    } else if (tid == 0) {
+      const uint32_t cw = ctr_word3(PURPOSE_LT, J.stream, j);
+      int32_t cur = root;
+      int tail = 1;
+      bool hit = s_hit != 0;
+      while (!hit) {
+        const int64_t lo = J.g.off[cur], hi = J.g.off[cur + 1];
+        if (hi == lo) break;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)cur, 0u, (uint32_t)j, cw), key);
+        const int32_t u = (int32_t)J.g.edge[lo + __umulhi(r.x, (uint32_t)(hi - lo))].x;
+        ev += 1;
+        const uint32_t mask = 1u << (u & 31);
+        if (bits[u >> 5] & mask) break;
+        bits[u >> 5] |= mask;
+        Q[tail++] = u;
+        if (MODE == MODE_HIT) hit = test_bit(J.seed_bits, (uint32_t)u);
+        cur = u;
+      }
+      s_tail = tail;
+      s_hit = hit;
+    }
+    __syncthreads();
+    const int tail = s_tail;
+    if (MODE == MODE_STORE) {
+      if (tid == 0) s_pos = atomicAdd(&J.ctr->cursor, (unsigned long long)tail);
+      __syncthreads();
+      const unsigned long long pos = s_pos;
+      if (pos + (unsigned long long)tail <= (unsigned long long)J.pool_cap) {
+        for (int i = tid; i < tail; i += nthr) {
+          J.pool_nodes[pos + i] = Q[i];
+          J.pool_samp[pos + i] = (int32_t)j;
+        }
+        if (tid == 0) {
+          J.set_start[j] = (int64_t)pos;
+          J.set_len[j] = tail;
+        }
+      } else if (tid == 0) {
+        atomicExch(&J.ctr->pool_overflow, 1u);
+      }
+    } else if (tid == 0) {
+      J.hit[j - J.j0] = s_hit ? 1 : 0;
+    }
+    if (tid == 0) nv += (unsigned long long)tail;
+    // reset the visited bits of this sample only
+    if ((int64_t)tail * 8 < J.bitmap_words) {
+      for (int i = tid; i < tail; i += nthr) bits[Q[i] >> 5] = 0u;
+    } else {
+      for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
+    }
+    __syncthreads();
+  }
+  flush_stats(J.ctr, ev, nv, lane, true);
+}
+
+}  // namespace
+
+constexpr int64_t SMEM_BITMAP_MAX_BYTES = 200 * 1024;
+
+LaunchCfg sampler_config(const GraphView& g, int model) {
+  LaunchCfg c;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  if (model == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE>, WT_WARPS * 32, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_lt<MODE_STORE>, WT_WARPS * 32, 0);
+  if (per_sm < 1) per_sm = 1;
+  c.warp_blocks = c.num_sms * per_sm;
+  const int64_t words = (g.n + 31) / 32;
+  c.smem_bitmap_bytes = words * 4;
+  c.cta_smem_bitmap = c.smem_bitmap_bytes <= SMEM_BITMAP_MAX_BYTES;
+  c.cta_threads = 1024;
+  c.cta_blocks = c.num_sms;
+  return c;
+}
+
+size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c) {
+  const size_t words = (size_t)((g.n + 31) / 32);
+  size_t per_slot = (size_t)g.n * 4 + (c.cta_smem_bitmap ? 0 : words * 4);
+  return per_slot * (size_t)c.cta_blocks;
+}
+
+cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
+  const dim3 grid(c.warp_blocks), block(WT_WARPS * 32);
+  if (J.model == 0) {
+    if (J.mode == MODE_STORE) k_sample_warp_ic<MODE_STORE><<<grid, block, 0, st>>>(J);
+    else k_sample_warp_ic<MODE_HIT><<<grid, block, 0, st>>>(J);
+  } else {
+    if (J.mode == MODE_STORE) k_sample_warp_lt<MODE_STORE><<<grid, block, 0, st>>>(J);
+    else k_sample_warp_lt<MODE_HIT><<<grid, block, 0, st>>>(J);
+  }
+  return cudaGetLastError();
+}
+
+template <int MODE, bool SB>
+static cudaError_t launch_cta_t(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
+  const size_t smem = SB ? (size_t)c.smem_bitmap_bytes : 0;
+  if (SB) {
+    cudaError_t e = cudaFuncSetAttribute(k_sample_cta<MODE, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_sample_cta<MODE, SB><<<c.cta_blocks, c.cta_threads, smem, st>>>(J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_cta(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
+  if (J.mode == MODE_STORE)
+    return c.cta_smem_bitmap ? launch_cta_t<MODE_STORE, true>(J, c, st) : launch_cta_t<MODE_STORE, false>(J, c, st);
+  return c.cta_smem_bitmap ? launch_cta_t<MODE_HIT, true>(J, c, st) : launch_cta_t<MODE_HIT, false>(J, c, st);
+}
+
+}  // namespace ssa

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the
+same seeded inputs, bit-exact for every integer result (CSR, thresholds, RR
+sets, counts, seed sets, coverage, Estimate-Inf T, round traces) and exactly
+equal FP64 influence (the 1e-12 relative bound is the stated tolerance)."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from gpu_common import c1_edges, sorted_sets
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_1605_07990_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1605_07990_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _pair(el, weighting=oracle.W_WC, thr=None, weight_seed=1):
+    og = oracle.Graph(el.n, el.src, el.dst, weighting, thr, weight_seed)
+    gg = P.ssa_load_graph(el.n, el.src, el.dst, thr, weighting, weight_seed)
+    return og, gg
+
+
+def _shuffled(el, seed=0):
+    rng = np.random.default_rng(seed)
+    p = rng.permutation(el.m)
+    return inputs.EdgeList(el.n, el.src[p].copy(), el.dst[p].copy())
+
+
+@pytest.mark.parametrize("weighting", [oracle.W_WC, oracle.W_TRIVALENCY, oracle.W_EXPLICIT])
+def test_graph_store(weighting):
+    el = _shuffled(inputs.rmat(12, 1 << 15, seed=2))
+    # duplicates and a self-loop kept as parallel edges
+    el = inputs.EdgeList(el.n, np.concatenate([el.src, el.src[:50], [7]]).astype(np.int32),
+                         np.concatenate([el.dst, el.dst[:50], [7]]).astype(np.int32))
+    thr = None
+    if weighting == oracle.W_EXPLICIT:
+        thr = np.random.default_rng(3).integers(0, 2**32, el.m, dtype=np.uint64).astype(np.uint32)
+    og, gg = _pair(el, weighting, thr, weight_seed=77)
+    o_off, o_src, o_thr = og.csr()
+    g_off, g_src, g_thr = P.ssa_graph_export(gg)
+    assert np.array_equal(o_off, g_off)
+    assert np.array_equal(o_src, g_src)
+    assert np.array_equal(o_thr, g_thr)
+
+
+def test_graph_rejects_bad_ids():
+    with pytest.raises(P.SSAError):
+        P.ssa_load_graph(4, np.array([0, 9], np.int32), np.array([1, 2], np.int32))
+
+
+def _check_pool(og, gg, model, seed, stream, N, benefit=None):
+    op = oracle.Pool(og, model, seed, stream, benefit).grow(N)
+    gp = P.Pool(gg, model, seed, stream, benefit).grow(N)
+    osets = op.sets()
+    gsets = gp.sets()
+    assert len(osets) == len(gsets) == N
+    bad = [j for j in range(N) if not np.array_equal(osets[j], gsets[j])]
+    assert not bad, f"{len(bad)} sets differ, first {bad[:5]}"
+    return op, gp
+
+
+@pytest.mark.parametrize("model", [oracle.IC, oracle.LT])
+def test_rr_sets_c1(model):
+    og, gg = _pair(c1_edges())
+    _check_pool(og, gg, model, seed=1, stream=0, N=12_345)
+
+
+def test_rr_sets_trivalency_cta_tier():
+    # trivalency IC on a 2^14-node R-MAT: bimodal sizes, large sets go to the CTA tier
+    el = inputs.rmat(14, 1 << 18, seed=5)
+    og, gg = _pair(el, oracle.W_TRIVALENCY)
+    op, gp = _check_pool(og, gg, oracle.IC, seed=9, stream=3, N=3001)
+    off, _ = op.arrays()
+    assert np.diff(off).max() > 512  # the CTA tier was exercised
+
+
+def test_rr_sets_p1_everything_large():
+    el = inputs.rmat(12, 1 << 14, seed=6)
+    thr = np.full(el.m, 0xFFFFFFFF, np.uint32)
+    og, gg = _pair(el, oracle.W_EXPLICIT, thr)
+    _check_pool(og, gg, oracle.IC, seed=4, stream=0, N=777)
+
+
+def test_rr_sets_wris():
+    el = c1_edges()
+    og, gg = _pair(el)
+    b = inputs.zipf_benefit(el.n, 1.2, seed=3)
+    for model in (oracle.IC, oracle.LT):
+        _check_pool(og, gg, model, seed=5, stream=1, N=4096 + 17, benefit=b)
+
+
+def test_rr_sets_empty_graph_and_isolated():
+    el = inputs.edges(100, [])
+    og, gg = _pair(el)
+    op, gp = _check_pool(og, gg, oracle.IC, seed=1, stream=0, N=1000)
+    assert all(len(s) == 1 for s in gp.sets())
+
+
+def test_counts_greedy_coverage_c1():
+    og, gg = _pair(c1_edges())
+    N = 2 * 2806
+    op, gp = _check_pool(og, gg, oracle.IC, seed=1, stream=0, N=N)
+    for Nsub in (2806, N, 1000):   # a batch boundary, the whole pool, and a cut inside a batch
+        assert np.array_equal(op.counts(Nsub), gp.counts(Nsub).astype(np.int64))
+        for k in (1, 50, 200):
+            os_, og_, oc = op.max_coverage(Nsub, k)
+            gs_, gg_, gc = gp.max_coverage(Nsub, k)
+            assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
+    S = os_[:37]
+    for a, b in ((0, N), (2806, N), (5, 1500)):
+        assert op.coverage(a, b, S) == gp.coverage(a, b - a, S)
+
+
+def test_greedy_k_equals_n():
+    el = inputs.rmat(6, 300, seed=1)
+    og, gg = _pair(el)
+    op, gp = _check_pool(og, gg, oracle.IC, seed=2, stream=0, N=500)
+    os_, og_, oc = op.max_coverage(500, el.n)
+    gs_, gg_, gc = gp.max_coverage(500, el.n)
+    assert np.array_equal(os_, gs_) and oc == gc == 500
+    assert sorted(gs_.tolist()) == list(range(el.n))
+
+
+@pytest.mark.parametrize("model", [oracle.IC, oracle.LT])
+def test_estimate_inf(model):
+    og, gg = _pair(c1_edges())
+    op = oracle.Pool(og, model, 1, 0).grow(3000)
+    S, _, _ = op.max_coverage(3000, 20)
+    for lam2, t_max in ((1500.7, 10**6), (800.0, 2000), (50.2, 10**5)):
+        oT, oh, _ = oracle.estimate_inf(og, model, 1, 5, S, lam2, t_max)
+        gT, gh = P.ssa_estimate_inf(gg, model, 1, 5, S, lam2, t_max)
+        assert (oT, oh) == (gT, gh)
+
+
+def _same_solution(o, g):
+    assert np.array_equal(o.seeds, g.seeds)
+    assert o.rounds == g.rounds
+    assert o.trace == g.trace
+    assert g.influence == pytest.approx(o.influence, rel=1e-12, abs=0)
+    assert o.n_rr == g.n_rr
+
+
+@pytest.mark.parametrize("algo,model", [(0, 0), (1, 0), (1, 1), (0, 1)])
+def test_solve_c1(algo, model):
+    # configuration 1 (SSA, WC-IC, k=50, eps=0.1, delta=1/n, Philox seed 1) plus the other three
+    # algorithm/model pairs on the same graph
+    el = c1_edges()
+    og, gg = _pair(el)
+    o = oracle.solve(og, algo, model, 50, 0.1, 1.0 / el.n, 1)
+    g = P.ssa_solve(gg, algo, model, 50, 0.1, 1.0 / el.n, 1)
+    _same_solution(o, g)
+
+
+def test_solve_wris_and_trivalency():
+    el = inputs.rmat(13, 1 << 16, seed=8)
+    og, gg = _pair(el, oracle.W_TRIVALENCY, weight_seed=5)
+    b = inputs.zipf_benefit(el.n, 1.2, seed=2)
+    for algo in (0, 1):
+        o = oracle.solve(og, algo, oracle.IC, 10, 0.2, 1.0 / el.n, 3, benefit=b)
+        g = P.ssa_solve(gg, algo, oracle.IC, 10, 0.2, 1.0 / el.n, 3, benefit=b)
+        _same_solution(o, g)
+
+
+def test_solver_reuse_same_answers():
+    el = c1_edges()
+    gg = P.ssa_load_graph(el.n, el.src, el.dst)
+    s = P.Solver(gg)
+    a = s.solve(1, 0, 10, 0.1, 1.0 / el.n, 11)
+    b = s.solve(1, 0, 10, 0.1, 1.0 / el.n, 11)
+    c = P.ssa_solve(gg, 1, 0, 10, 0.1, 1.0 / el.n, 11)
+    assert np.array_equal(a.seeds, b.seeds) and a.trace == b.trace == c.trace
+
+
+def test_bad_solve_arguments():
+    el = c1_edges()
+    gg = P.ssa_load_graph(el.n, el.src, el.dst, None, P.SSA_W_TRIVALENCY)
+    with pytest.raises(P.SSAError):
+        P.ssa_solve(gg, 1, 1, 10, 0.1, 0.01, 1)  # LT needs WC weights
+    with pytest.raises(P.SSAError):
+        P.ssa_solve(gg, 1, 0, 0, 0.1, 0.01, 1)
+    with pytest.raises(P.SSAError):
+        P.ssa_solve(gg, 1, 0, 10, 0.9, 0.01, 1)
+
+
+def test_pool_cap_reports_pool_full():
+    el = c1_edges()
+    gg = P.ssa_load_graph(el.n, el.src, el.dst)
+    with pytest.raises(P.SSAError) as e:
+        P.ssa_solve(gg, 1, 0, 50, 0.1, 1.0 / el.n, 1, pool_bytes_cap=200_000)
+    assert e.value.status == 3
