@@ -198,6 +198,9 @@ struct Sampler {
   Counters* h_ctr = nullptr;  // pinned
   int64_t* big_list = nullptr;
   int64_t big_cap = 0;
+  int64_t* fail_list = nullptr;  // samples whose pool reservation did not fit
+  int64_t* redo_list = nullptr;  // the previous attempt's fail list, re-run
+  int64_t fail_cap = 0, redo_cap = 0;
   uint32_t* slot_bitmap = nullptr;
   int32_t* slot_queue = nullptr;
   uint8_t* hit = nullptr;
@@ -247,6 +250,8 @@ struct Sampler {
     if (h_ctr) cudaFreeHost(h_ctr);
     h_ctr = nullptr;
     dev_free(big_list, st);
+    dev_free(fail_list, st);
+    dev_free(redo_list, st);
     dev_free(slot_bitmap, st);
     dev_free(slot_queue, st);
     dev_free(hit, st);
@@ -268,6 +273,15 @@ struct Sampler {
     J.slot_queue = slot_queue;
     J.bitmap_words = (g.n + 31) / 32;
     J.ctr = d_ctr;
+    J.fail_list = fail_list;
+    // Philox4x32-10 key schedule: round r uses key + r * (0x9E3779B9, 0xBB67AE85)
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+      J.rk[2 * r] = k0;
+      J.rk[2 * r + 1] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
     return J;
   }
 
@@ -289,11 +303,21 @@ struct Sampler {
   }
 
   // Append samples [pool.count, pool.count + count) of (seed, stream) to the pool.
+  // The pool is sized from the mean set size seen so far (a 1024-sample pilot
+  // batch measures it when the pool is empty); samples whose reservation still
+  // does not fit are listed by the kernels and re-run after the pool grows, so
+  // no finished set is sampled twice.
   ssa_status append(DevPool& P, uint64_t seed, uint32_t stream, int64_t count, Exec& X) {
     if (count <= 0) return SSA_OK;
+    if (P.count == 0 && count > 4096) {
+      TRY(append(P, seed, stream, 1024, X));
+      count -= 1024;
+    }
     const int64_t j0 = P.count;
     if (j0 + count > (int64_t)0x7FFFFFFF) return fail(SSA_E_POOL_FULL, "more than 2^31 RR sets");
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&fail_list, &fail_cap, count, 0, X.st));
+    TRY(dev_grow(&redo_list, &redo_cap, count, 0, X.st));
     if (j0 + count > P.cap_sets) {
       int64_t want = std::max<int64_t>(j0 + count, P.cap_sets * 2);
       int64_t c1 = P.cap_sets, c2 = P.cap_sets;
@@ -301,43 +325,70 @@ struct Sampler {
       TRY(dev_grow(&P.set_len, &c2, want, j0, X.st));
       P.cap_sets = want;
     }
-    if (P.cap_entries == 0) {
-      int64_t want = std::max<int64_t>(1 << 20, count * 16);
-      if (P.byte_cap > 0) want = std::max<int64_t>(1, std::min<int64_t>(want, (P.byte_cap - P.cap_sets * 14) / 12));
-      int64_t a = 0, b = 0;
-      TRY(dev_grow(&P.nodes, &a, want, 0, X.st));
-      TRY(dev_grow(&P.samp, &b, want, 0, X.st));
-      P.cap_entries = want;
-    }
-    for (int attempt = 0; attempt < 64; ++attempt) {
-      SampleJob J = job(seed, stream, j0, count);
+    const double mean = P.count > 0 ? (double)P.entries / (double)P.count : 16.0;
+    int64_t want = P.entries + (int64_t)(mean * (double)count * 1.15) + 65536;
+    TRY(grow_entries(P, want, X));
+    int64_t todo = count;
+    const int64_t* list = nullptr;
+    unsigned long long cursor0 = (unsigned long long)P.entries;
+    unsigned long long ev = 0, nv = 0, cev = 0, cnv = 0, csets = 0;
+    for (int attempt = 0; todo > 0; ++attempt) {
+      if (attempt >= 64) return fail(SSA_E_INTERNAL, "pool growth did not converge");
+      SampleJob J = job(seed, stream, j0, todo);
+      J.work_list = list;
       J.mode = MODE_STORE;
       J.pool_nodes = P.nodes;
       J.pool_samp = P.samp;
       J.pool_cap = P.cap_entries;
       J.set_start = P.set_start;
       J.set_len = P.set_len;
-      TRY(run(J, X, (unsigned long long)P.entries));
-      if (!h_ctr->pool_overflow) break;
-      // the cursor kept counting past the cap: grow to what the batch needs and redo it
-      const int64_t need = (int64_t)h_ctr->cursor;
-      int64_t want = std::max<int64_t>(need + need / 4, P.cap_entries * 2);
-      if (P.byte_cap > 0 && P.bytes_for(want, P.cap_sets) > P.byte_cap) {
-        want = need;
-        if (P.bytes_for(want, P.cap_sets) > P.byte_cap)
-          return fail(SSA_E_POOL_FULL, "RR pool needs %lld entries, over the %lld-byte cap", (long long)need,
-                      (long long)P.byte_cap);
+      TRY(run(J, X, cursor0));
+      ev += h_ctr->edge_visits;
+      nv += h_ctr->node_visits;
+      cev += h_ctr->cta_edge_visits;
+      cnv += h_ctr->cta_node_visits;
+      csets += h_ctr->big_count;
+      if (!h_ctr->pool_overflow) {
+        cursor0 = h_ctr->cursor;
+        break;
       }
-      int64_t a = P.cap_entries, b = P.cap_entries;
-      TRY(dev_grow(&P.nodes, &a, want, P.entries, X.st));
-      TRY(dev_grow(&P.samp, &b, want, P.entries, X.st));
-      P.cap_entries = want;
+      // [ok_end, cursor) were reserved by samples that did not fit: re-run them
+      const int64_t ok_end = (int64_t)std::max<unsigned long long>(h_ctr->ok_end, cursor0);
+      const int64_t need = (int64_t)h_ctr->cursor - ok_end;
+      const int64_t failed = (int64_t)h_ctr->fail_count;
+      P.entries = ok_end;
+      TRY(grow_entries(P, ok_end + need + need / 4 + 65536, X));
+      std::swap(fail_list, redo_list);
+      std::swap(fail_cap, redo_cap);
+      list = redo_list;
+      todo = failed;
+      cursor0 = (unsigned long long)ok_end;
     }
-    if (h_ctr->pool_overflow) return fail(SSA_E_INTERNAL, "pool growth did not converge");
-    tally(count);
-    P.entries = (int64_t)h_ctr->cursor;
+    edge_visits += (int64_t)ev;
+    node_visits += (int64_t)nv;
+    cta_edge_visits += (int64_t)cev;
+    cta_node_visits += (int64_t)cnv;
+    cta_samples += (int64_t)csets;
+    samples += count;
+    P.entries = (int64_t)cursor0;
     P.count = j0 + count;
     P.bounds.emplace_back(P.count, P.entries);
+    return SSA_OK;
+  }
+
+  ssa_status grow_entries(DevPool& P, int64_t want, Exec& X) {
+    if (want <= P.cap_entries) return SSA_OK;
+    want = std::max<int64_t>(want, P.cap_entries + P.cap_entries / 2);
+    if (P.byte_cap > 0 && P.bytes_for(want, P.cap_sets) > P.byte_cap) {
+      const int64_t most = (P.byte_cap - P.cap_sets * 14) / 12;
+      if (most <= P.cap_entries)
+        return fail(SSA_E_POOL_FULL, "RR pool needs more than its %lld-byte cap", (long long)P.byte_cap);
+      want = most;
+    }
+    int64_t a = P.cap_entries, b = P.cap_entries;
+    TRY(dev_grow(&P.nodes, &a, want, P.entries, X.st));
+    TRY(dev_grow(&P.samp, &b, want, P.entries, X.st));
+    P.cap_entries = want;
     return SSA_OK;
   }
 

@@ -25,6 +25,8 @@ struct Counters {
   unsigned long long node_visits;  // nodes added to RR sets
   unsigned long long cta_edge_visits;  // the CTA tier's share of the two above
   unsigned long long cta_node_visits;
+  unsigned long long ok_end;        // end of the last pool reservation that fit
+  unsigned long long fail_count;    // samples whose reservation did not fit (listed in fail_list)
   unsigned int pool_overflow;      // a reservation passed pool_cap
   unsigned int error;              // internal error flag
 };
@@ -36,7 +38,10 @@ struct SampleJob {
   int model = 0;                 // 0 IC, 1 LT
   uint64_t seed = 0;
   uint32_t stream = 0;
-  int64_t j0 = 0, count = 0;     // samples [j0, j0+count)
+  int64_t j0 = 0, count = 0;     // samples [j0, j0+count), or work_list[0, count)
+  const int64_t* work_list = nullptr;  // explicit sample ids (re-run of pool overflows) or null
+  int64_t* fail_list = nullptr;        // samples whose pool reservation did not fit
+  uint32_t rk[20] = {};                // Philox round keys: rk[2r], rk[2r+1] = key + r * Weyl
   const uint64_t* bprefix = nullptr;  // WRIS prefix sums (n+1) or null
   int mode = MODE_STORE;
   // MODE_STORE: flat pool entries + per-sample extents

@@ -10,7 +10,11 @@
 // IC frontier expansion is edge-balanced inside a warp: 32 frontier nodes'
 // in-edge ranges are cut into 4-edge groups (the unit of one Philox draw, one
 // aligned 32-byte sector of {src,thr} records) and the groups are dealt to
-// lanes by a warp prefix sum.
+// lanes by a warp prefix sum.  The kernel is bound by integer issue (Philox),
+// so the expansion (a) takes the Philox round keys from the kernel parameters,
+// (b) in the CTA tier skips the draw of a group whose live-able edges all
+// come from already-visited nodes (such an edge cannot change the set), and
+// (c) compacts the live candidates of a 128-edge slab into one insert round.
 #include "device.cuh"
 
 namespace ssa {
@@ -21,6 +25,40 @@ constexpr int WT_WARPS = 8;      // warps per warp-tier block
 constexpr int WT_HASH = 1024;    // hash slots per warp (power of two)
 constexpr int WT_QCAP = 512;     // largest IC set kept in the warp tier
 constexpr int LT_QCAP = 1024;    // largest LT walk kept in the warp tier
+constexpr int STAGE = 128;       // live candidates of one slab (32 lanes x 4 edges)
+
+constexpr uint32_t PHILOX_M0 = 0xD2511F53u, PHILOX_M1 = 0xCD9E8D57u;
+
+// Philox4x32-10 of the counter (x, 0, jlo, cw) with the per-launch round keys
+// rk; s0/s1/s2 carry the sample-constant parts of the first round:
+// s0 = hi(M1*jlo) ^ rk[0], s1 = lo(M1*jlo), s2 = cw ^ rk[1].
+struct SampleConst {
+  uint32_t s0, s1, s2;
+};
+
+__device__ __forceinline__ SampleConst sample_const(const uint32_t* rk, uint32_t jlo, uint32_t cw) {
+  SampleConst c;
+  c.s0 = __umulhi(PHILOX_M1, jlo) ^ rk[0];
+  c.s1 = PHILOX_M1 * jlo;
+  c.s2 = cw ^ rk[1];
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_x(uint32_t x, const SampleConst& sc, const uint32_t* rk) {
+  // round 1 with c.y = 0 and the sample constants folded in
+  uint4 c = make_uint4(sc.s0, sc.s1, __umulhi(PHILOX_M0, x) ^ sc.s2, PHILOX_M0 * x);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t lo0 = PHILOX_M0 * c.x, hi0 = __umulhi(PHILOX_M0, c.x);
+    const uint32_t lo1 = PHILOX_M1 * c.z, hi1 = __umulhi(PHILOX_M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ int64_t sample_at(const SampleJob& J, unsigned long long idx) {
+  return J.work_list ? J.work_list[idx] : J.j0 + (int64_t)idx;
+}
 
 __device__ __forceinline__ int32_t pick_root(const SampleJob& J, int64_t j) {
   const uint4 r = keyed_draw(J.seed, PURPOSE_ROOT, J.stream, j, 0);
@@ -54,22 +92,25 @@ __device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u) {
 }
 
 // Edge-balanced expansion of up to 32 frontier nodes (lane i holds node v or
-// -1).  For each live in-edge the lane holding it gets visit(u, true); every
-// lane calls visit 4 times per 32-group slab (uniform control flow), and the
-// expansion stops early when visit returns true (must be warp-uniform).
-template <class Visit>
-__device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, uint2 key, uint32_t jlo, uint32_t cw,
-                                          int lane, unsigned long long& ev, Visit&& visit) {
-  int64_t lo = 0, hi = 0;
+// -1).  Live in-edges whose tail may be new are compacted through `stage`
+// (STAGE entries, private to the warp) and handed to visit(u) in rounds of 32
+// (NO_NODE for idle lanes); visit returns a warp-uniform "stop".  known(u)
+// may report nodes already in the set so their edges need no draw.
+template <class Known, class Visit>
+__device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
+                                          int lane, uint32_t* stage, unsigned long long& ev, Known&& known,
+                                          Visit&& visit) {
+  uint32_t lo = 0, hi = 0;  // edge positions fit 32 bits (m < 2^31)
   if (v >= 0) {
-    lo = __ldg(g.off + v);
-    hi = __ldg(g.off + v + 1);
+    lo = (uint32_t)__ldg(g.off + v);
+    hi = (uint32_t)__ldg(g.off + v + 1);
   }
-  ev += (unsigned long long)(hi - lo);
+  ev += hi - lo;
   const int ng = (hi > lo) ? (int)(((hi + 3) >> 2) - (lo >> 2)) : 0;
   const int incl = warp_inclusive_scan(ng, lane);
   const int excl = incl - ng;
   const int total = __shfl_sync(FULL_MASK, incl, 31);
+  const unsigned lt_mask = (1u << lane) - 1u;
   for (int base = 0; base < total; base += 32) {
     const int q = base + lane;
     int owner = 0;
@@ -79,25 +120,50 @@ __device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, uint2 k
       if (t <= q) owner += s;
     }
     owner = owner > 31 ? 31 : owner;
-    const int64_t olo = __shfl_sync(FULL_MASK, lo, owner);
-    const int64_t ohi = __shfl_sync(FULL_MASK, hi, owner);
+    const uint32_t olo = __shfl_sync(FULL_MASK, lo, owner);
+    const uint32_t ohi = __shfl_sync(FULL_MASK, hi, owner);
     const int oex = __shfl_sync(FULL_MASK, excl, owner);
-    uint32_t c0 = NO_NODE, c1 = NO_NODE, c2 = NO_NODE, c3 = NO_NODE;
+    uint32_t cand = 0, u0 = 0, u1 = 0, u2 = 0, u3 = 0;
     if (q < total) {
-      const int64_t grp = (olo >> 2) + (q - oex);
-      const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)(grp >> 32), jlo, cw), key);
-      const uint4* p = reinterpret_cast<const uint4*>(g.edge) + grp * 2;
-      const uint4 a = __ldg(p), b = __ldg(p + 1);
-      const int64_t e = grp * 4;
-      if (e >= olo && e < ohi && edge_live(r.x, a.y)) c0 = a.x;
-      if (e + 1 >= olo && e + 1 < ohi && edge_live(r.y, a.w)) c1 = a.z;
-      if (e + 2 >= olo && e + 2 < ohi && edge_live(r.z, b.y)) c2 = b.x;
-      if (e + 3 >= olo && e + 3 < ohi && edge_live(r.w, b.w)) c3 = b.z;
+      const uint32_t grp = (olo >> 2) + (uint32_t)(q - oex);
+      const uint32_t e = grp * 4u;
+      // edges e..e+3 that belong to the owner's in-list
+      const uint32_t a = olo > e ? olo - e : 0u;
+      const uint32_t b = ohi - e;
+      uint32_t need = (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
+      const uint4* p = reinterpret_cast<const uint4*>(g.edge) + (size_t)grp * 2;
+      const uint4 A = __ldg(p), B = __ldg(p + 1);
+      u0 = A.x; u1 = A.z; u2 = B.x; u3 = B.z;
+      if ((need & 1u) && known(u0)) need &= ~1u;
+      if ((need & 2u) && known(u1)) need &= ~2u;
+      if ((need & 4u) && known(u2)) need &= ~4u;
+      if ((need & 8u) && known(u3)) need &= ~8u;
+      if (need) {
+        const uint4 r = philox_x(grp, sc, rk);
+        if ((need & 1u) && edge_live(r.x, A.y)) cand |= 1u;
+        if ((need & 2u) && edge_live(r.y, A.w)) cand |= 2u;
+        if ((need & 4u) && edge_live(r.z, B.y)) cand |= 4u;
+        if ((need & 8u) && edge_live(r.w, B.w)) cand |= 8u;
+      }
     }
-    if (visit(c0)) return true;
-    if (visit(c1)) return true;
-    if (visit(c2)) return true;
-    if (visit(c3)) return true;
+    const unsigned any = __ballot_sync(FULL_MASK, cand != 0u);
+    if (!any) continue;
+    const int c = __popc(cand);
+    const int cin = warp_inclusive_scan(c, lane);
+    const int ctot = __shfl_sync(FULL_MASK, cin, 31);
+    int pos = cin - c;
+    if (cand & 1u) stage[pos++] = u0;
+    if (cand & 2u) stage[pos++] = u1;
+    if (cand & 4u) stage[pos++] = u2;
+    if (cand & 8u) stage[pos++] = u3;
+    __syncwarp();
+    bool stop = false;
+    for (int s0 = 0; s0 < ctot && !stop; s0 += 32) {
+      const uint32_t u = (s0 + lane < ctot) ? stage[s0 + lane] : NO_NODE;
+      stop = visit(u, lt_mask);
+    }
+    __syncwarp();
+    if (stop) return true;
   }
   return false;
 }
@@ -114,24 +180,36 @@ __device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev
   }
 }
 
-// Store a finished set of `size` nodes held in Q (shared or global) for the
-// warp starting at lane 0.. ; returns nothing, flags pool overflow.
+// Reserve `size` pool entries (one thread).  Reservations are handed out in
+// increasing position order, so the ones that fit form a prefix ending at
+// ok_end and the rest [ok_end, cursor) are re-run by the host from fail_list.
+__device__ __forceinline__ bool reserve(const SampleJob& J, int64_t j, int size, unsigned long long* pos) {
+  *pos = atomicAdd(&J.ctr->cursor, (unsigned long long)size);
+  if (*pos + (unsigned long long)size <= (unsigned long long)J.pool_cap) {
+    atomicMax(&J.ctr->ok_end, *pos + (unsigned long long)size);
+    return true;
+  }
+  atomicExch(&J.ctr->pool_overflow, 1u);
+  const unsigned long long f = atomicAdd(&J.ctr->fail_count, 1ull);
+  J.fail_list[f] = j;
+  return false;
+}
+
 template <typename QT>
 __device__ __forceinline__ void warp_store_set(const SampleJob& J, int64_t j, const QT* Q, int size, int lane) {
   unsigned long long pos = 0;
-  if (lane == 0) pos = atomicAdd(&J.ctr->cursor, (unsigned long long)size);
+  int ok = 0;
+  if (lane == 0) ok = reserve(J, j, size, &pos);
+  ok = __shfl_sync(FULL_MASK, ok, 0);
   pos = __shfl_sync(FULL_MASK, pos, 0);
-  if (pos + (unsigned long long)size <= (unsigned long long)J.pool_cap) {
-    for (int i = lane; i < size; i += 32) {
-      J.pool_nodes[pos + i] = Q[i];
-      J.pool_samp[pos + i] = (int32_t)j;
-    }
-    if (lane == 0) {
-      J.set_start[j] = (int64_t)pos;
-      J.set_len[j] = size;
-    }
-  } else if (lane == 0) {
-    atomicExch(&J.ctr->pool_overflow, 1u);
+  if (!ok) return;
+  for (int i = lane; i < size; i += 32) {
+    J.pool_nodes[pos + i] = Q[i];
+    J.pool_samp[pos + i] = (int32_t)j;
+  }
+  if (lane == 0) {
+    J.set_start[j] = (int64_t)pos;
+    J.set_len[j] = size;
   }
 }
 
@@ -139,22 +217,21 @@ template <int MODE>
 __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
   __shared__ __align__(16) uint32_t s_hash[WT_WARPS][WT_HASH];
   __shared__ int32_t s_q[WT_WARPS][WT_QCAP];
+  __shared__ uint32_t s_stage[WT_WARPS][STAGE];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t* H = s_hash[wid];
   int32_t* Q = s_q[wid];
   uint4* H4 = reinterpret_cast<uint4*>(H);
-  const unsigned lt_mask = (1u << lane) - 1u;
   for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
   __syncwarp();
-  const uint2 key = philox_key(J.seed);
   unsigned long long ev = 0, nv = 0;
   for (;;) {
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= (unsigned long long)J.count) break;
-    const int64_t j = J.j0 + (int64_t)idx;
-    const uint32_t cw = ctr_word3(PURPOSE_IC, J.stream, j);
+    const int64_t j = sample_at(J, idx);
+    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) {
       H[hash_slot((uint32_t)root)] = (uint32_t)root + 1u;
@@ -164,7 +241,8 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
     bool overflow = false;
     bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
     __syncwarp();
-    auto visit = [&](uint32_t u) -> bool {
+    auto known = [](uint32_t) { return false; };
+    auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
       const bool is_new = (u != NO_NODE) && hash_insert(H, u);
       const unsigned m = __ballot_sync(FULL_MASK, is_new);
       bool h = false;
@@ -183,7 +261,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      expand_ic(J.g, v, key, (uint32_t)j, cw, lane, ev, visit);
+      expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, known, visit);
       head += cnt;
     }
     __syncwarp();
@@ -194,7 +272,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       }
     } else {
       if (MODE == MODE_STORE) warp_store_set(J, j, Q, tail, lane);
-      else if (lane == 0) J.hit[idx] = hit ? 1 : 0;
+      else if (lane == 0) J.hit[j - J.j0] = hit ? 1 : 0;
       if (lane == 0) nv += (unsigned long long)tail;
     }
     __syncwarp();
@@ -212,15 +290,14 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
   __shared__ int32_t s_q[WT_WARPS][LT_QCAP];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* Q = s_q[wid];
-  const uint2 key = philox_key(J.seed);
   unsigned long long ev = 0, nv = 0;
   for (;;) {
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= (unsigned long long)J.count) break;
-    const int64_t j = J.j0 + (int64_t)idx;
-    const uint32_t cw = ctr_word3(PURPOSE_LT, J.stream, j);
+    const int64_t j = sample_at(J, idx);
+    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_LT, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) Q[0] = root;
     int tail = 1;
@@ -232,7 +309,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
       const int64_t lo = __ldg(J.g.off + cur), hi = __ldg(J.g.off + cur + 1);
       const int64_t d = hi - lo;
       if (d == 0) break;
-      const uint4 r = philox4x32_10(make_uint4((uint32_t)cur, 0u, (uint32_t)j, cw), key);
+      const uint4 r = philox_x((uint32_t)cur, sc, J.rk);
       const int32_t u = (int32_t)__ldg(&J.g.edge[lo + __umulhi(r.x, (uint32_t)d)].x);
       if (lane == 0) ev += 1;
       bool found = false;
@@ -256,7 +333,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
       }
     } else {
       if (MODE == MODE_STORE) warp_store_set(J, j, Q, tail, lane);
-      else if (lane == 0) J.hit[idx] = hit ? 1 : 0;
+      else if (lane == 0) J.hit[j - J.j0] = hit ? 1 : 0;
       if (lane == 0) nv += (unsigned long long)tail;
     }
     __syncwarp();
@@ -269,16 +346,16 @@ template <int MODE, bool SMEM_BITMAP>
 __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
   extern __shared__ __align__(16) uint32_t s_bits[];
   __shared__ long long s_item;
-  __shared__ int s_tail, s_next, s_hit;
+  __shared__ int s_tail, s_next, s_hit, s_ok;
   __shared__ unsigned long long s_pos;
+  __shared__ uint32_t s_stage[32][STAGE];
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
-  const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t n = J.g.n;
   uint32_t* bits = SMEM_BITMAP ? s_bits : J.slot_bitmap + (size_t)blockIdx.x * (size_t)J.bitmap_words;
   int32_t* Q = J.slot_queue + (size_t)blockIdx.x * (size_t)n;
+  uint32_t* stage = s_stage[tid >> 5];
   if (SMEM_BITMAP)
     for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
-  const uint2 key = philox_key(J.seed);
   const long long big_count = (long long)*((volatile unsigned long long*)&J.ctr->big_count);
   unsigned long long ev = 0, nv = 0;
   __syncthreads();
@@ -297,7 +374,27 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
     }
     __syncthreads();
     if (J.model == 0) {
-      const uint32_t cw = ctr_word3(PURPOSE_IC, J.stream, j);
+      const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
+      auto known = [&](uint32_t u) { return ((*(volatile uint32_t*)(bits + (u >> 5))) >> (u & 31)) & 1u; };
+      auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
+        bool is_new = false;
+        if (u != NO_NODE) {
+          const uint32_t mask = 1u << (u & 31);
+          is_new = !(atomicOr(bits + (u >> 5), mask) & mask);
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, is_new);
+        if (m) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
+          base = __shfl_sync(FULL_MASK, base, 0);
+          if (is_new) {
+            Q[base + __popc(m & lt_mask)] = (int32_t)u;
+            if (MODE == MODE_HIT && test_bit(J.seed_bits, u)) s_hit = 1;
+          }
+        }
+        if (MODE == MODE_HIT) return __any_sync(FULL_MASK, *(volatile int*)&s_hit != 0);
+        return false;
+      };
       int lvl_begin = 0, lvl_end = 1;
       for (;;) {
         // every thread is past the previous barrier and nobody writes s_hit
@@ -312,26 +409,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
           if (b >= lvl_end) break;
           const int cnt = min(32, lvl_end - b);
           const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
-          auto visit = [&](uint32_t u) -> bool {
-            bool is_new = false;
-            if (u != NO_NODE) {
-              const uint32_t mask = 1u << (u & 31);
-              is_new = !(atomicOr(bits + (u >> 5), mask) & mask);
-            }
-            const unsigned m = __ballot_sync(FULL_MASK, is_new);
-            if (m) {
-              int base = 0;
-              if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
-              base = __shfl_sync(FULL_MASK, base, 0);
-              if (is_new) {
-                Q[base + __popc(m & lt_mask)] = (int32_t)u;
-                if (MODE == MODE_HIT && test_bit(J.seed_bits, u)) s_hit = 1;
-              }
-            }
-            if (MODE == MODE_HIT) return __any_sync(FULL_MASK, *(volatile int*)&s_hit != 0);
-            return false;
-          };
-          if (expand_ic(J.g, v, key, (uint32_t)j, cw, lane, ev, visit)) break;
+          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, known, visit)) break;
         }
         __syncthreads();
         lvl_begin = lvl_end;
@@ -339,14 +417,14 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
         __syncthreads();
       }
     } else if (tid == 0) {
-      const uint32_t cw = ctr_word3(PURPOSE_LT, J.stream, j);
+      const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_LT, J.stream, j));
       int32_t cur = root;
       int tail = 1;
       bool hit = s_hit != 0;
       while (!hit) {
         const int64_t lo = J.g.off[cur], hi = J.g.off[cur + 1];
         if (hi == lo) break;
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)cur, 0u, (uint32_t)j, cw), key);
+        const uint4 r = philox_x((uint32_t)cur, sc, J.rk);
         const int32_t u = (int32_t)J.g.edge[lo + __umulhi(r.x, (uint32_t)(hi - lo))].x;
         ev += 1;
         const uint32_t mask = 1u << (u & 31);
@@ -362,10 +440,14 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
     __syncthreads();
     const int tail = s_tail;
     if (MODE == MODE_STORE) {
-      if (tid == 0) s_pos = atomicAdd(&J.ctr->cursor, (unsigned long long)tail);
+      if (tid == 0) {
+        unsigned long long pos = 0;
+        s_ok = reserve(J, j, tail, &pos);
+        s_pos = pos;
+      }
       __syncthreads();
-      const unsigned long long pos = s_pos;
-      if (pos + (unsigned long long)tail <= (unsigned long long)J.pool_cap) {
+      if (s_ok) {
+        const unsigned long long pos = s_pos;
         for (int i = tid; i < tail; i += nthr) {
           J.pool_nodes[pos + i] = Q[i];
           J.pool_samp[pos + i] = (int32_t)j;
@@ -374,8 +456,6 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
           J.set_start[j] = (int64_t)pos;
           J.set_len[j] = tail;
         }
-      } else if (tid == 0) {
-        atomicExch(&J.ctr->pool_overflow, 1u);
       }
     } else if (tid == 0) {
       J.hit[j - J.j0] = s_hit ? 1 : 0;
@@ -394,7 +474,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
 
 }  // namespace
 
-constexpr int64_t SMEM_BITMAP_MAX_BYTES = 200 * 1024;
+constexpr int64_t SMEM_BITMAP_MAX_BYTES = 192 * 1024;
 
 LaunchCfg sampler_config(const GraphView& g, int model) {
   LaunchCfg c;
