@@ -210,6 +210,38 @@ ssa_status ssa_estimate_inf(const ssa_graph* g, ssa_model model, uint64_t seed, 
                             const uint32_t* benefit, const int32_t* seeds, int32_t k, double lambda2,
                             int64_t t_max, int64_t* T, int64_t* hits);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free coverage count (no counterpart in the paper).            */
+/* ------------------------------------------------------------------------ */
+
+/* Same count as ssa_coverage -- the number of RR sets with a sample id in
+ * [first, first+count) that contain at least one seed -- over a flat RR pool
+ * the caller holds in device memory, for callers that cannot allocate device
+ * memory when they call: for example a serving loop that reserved all of its
+ * device memory up front, or a host runtime whose own allocator owns the
+ * device.  It calls no cudaMalloc/cudaFree or allocating library routine; its
+ * scratch is one fixed 16 MiB device array inside the library, held on every
+ * device that loads the library until the process exits.
+ *   n        node count (node and seed ids lie in [0, n))
+ *   nodes    device int32[entries]: node of each pool entry
+ *   samp     device int32[entries]: sample id of each pool entry (entries of
+ *            one sample need not be contiguous; other samples are ignored)
+ *   seeds    device int32[k]
+ *   cov      host out: the count
+ *   stream   cudaStream_t to run on (NULL = the legacy default stream); the
+ *            call synchronises that stream before returning.
+ * Limit: n/32 + count/32 32-bit words plus a 256-byte header must fit the
+ * 16 MiB array (n + count below about 134 million), else SSA_E_ARG.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * once, so make that first call before any stream capture.  Every call shares
+ * the one array and clears the part it uses; calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Errors: SSA_E_ARG (sizes, null pointers, ids outside [0, n)),
+ * SSA_E_CUDA. */
+ssa_status ssa_coverage_noalloc(int64_t n, const int32_t* nodes, const int32_t* samp, int64_t entries,
+                                int64_t first, int64_t count, const int32_t* seeds, int32_t k,
+                                int64_t* cov, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ EXPORTS = {
     "ssa_coverage": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]),
     "ssa_estimate_inf": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
                                    C.c_int32, C.c_double, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ssa_coverage_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                       C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -344,3 +346,12 @@ def ssa_estimate_inf(g: Graph, model, seed, stream, S, lambda2, t_max, benefit=N
     _check(lib().ssa_estimate_inf(g.h, int(model), _u64(seed), int(stream), _ptr(b), _ptr(S), int(S.shape[0]),
                                   float(lambda2), int(t_max), C.byref(T), C.byref(hits)))
     return T.value, hits.value
+
+
+def ssa_coverage_noalloc(n, nodes_ptr, samp_ptr, entries, first, count, seeds_ptr, k, stream=None):
+    """Allocation-free Cov over a caller-held device pool.  *_ptr are device
+    addresses (e.g. torch tensor .data_ptr()); stream a cudaStream_t or None."""
+    cov = C.c_int64()
+    _check(lib().ssa_coverage_noalloc(int(n), nodes_ptr, samp_ptr, int(entries), int(first), int(count),
+                                      seeds_ptr, int(k), C.byref(cov), stream))
+    return cov.value

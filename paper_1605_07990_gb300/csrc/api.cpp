@@ -71,6 +71,15 @@ ssa_status dev_grow(T** p, int64_t* cap, int64_t want, int64_t keep, cudaStream_
   return SSA_OK;
 }
 
+}  // namespace
+
+// Lets other translation units of the library report an error message.
+void ssa::set_last_error(const char* msg) {
+  std::strncpy(g_err, msg, sizeof(g_err) - 1);
+  g_err[sizeof(g_err) - 1] = 0;
+}
+
+namespace {
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }

@@ -6,6 +6,9 @@
 
 namespace ssa {
 
+// Sets the calling thread's message returned by ssa_last_error().
+void set_last_error(const char* msg);
+
 // Device-resident in-edge CSR (Sec. 2).  Edge records interleave the tail
 // node and the uint32 live threshold so one 8-byte load serves an edge and a
 // 4-edge group (the unit of one Philox draw) is one aligned 32-byte sector.
