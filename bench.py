@@ -167,6 +167,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sets", type=int, default=150)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sample-only", type=int, default=0,
+                    help="profiling case: only sample this many RR sets of the workload into a pool")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -188,6 +190,13 @@ def main():
     el, weighting, algo, model, k, eps = make_graph_inputs(name)
     delta = 1.0 / el.n
     g = P.ssa_load_graph(el.n, el.src, el.dst, None, weighting, 1)
+    if args.sample_only:
+        pool = P.Pool(g, model, seed=1, stream=0).grow(args.sample_only)
+        torch.cuda.synchronize()
+        print(json.dumps({"sample_only": args.sample_only, "pool": pool.info()}))
+        pool.free()
+        g.free()
+        return 0
     stream = torch.cuda.current_stream()
     solver = P.Solver(g, stream=stream.cuda_stream)
 
@@ -237,13 +246,13 @@ def main():
     cta_ev = sum(r.cta_edge_visits for r in results)
     cta_nv = sum(r.cta_node_visits for r in results)
     cta_sets = sum(r.cta_sets for r in results)
-    # algorithmic bytes: 8 per examined in-edge ({src,thr}), 16 per visited node (two CSR offsets)
-    # + 8 per stored pool entry (node, sample id), 12 per stored set (start, length)
-    stored = sum(r.pool_entries for r in results)
+    cta_st_e = sum(r.cta_stored_entries for r in results)
+    cta_st_s = sum(r.cta_stored_sets for r in results)
+    # algorithmic bytes of the CTA-tier sampler: 8 per examined in-edge ({src,thr} record), 16 per
+    # visited node (its two CSR offsets), 8 per stored pool entry (node, sample id), 12 per stored
+    # set (start, length), 1 per hit-tested set (its flag)
     if dom == "sample_cta":
-        abytes = 8 * cta_ev + 24 * cta_nv + 12 * cta_sets
-    elif dom == "sample_warp":
-        abytes = 8 * (ev - cta_ev) + 16 * (nv - cta_nv) + 8 * (stored - cta_nv) + 12 * sum(r.n_rr for r in results)
+        abytes = 8 * cta_ev + 16 * cta_nv + 8 * cta_st_e + 12 * cta_st_s + (cta_sets - cta_st_s)
     else:
         abytes = None
     peak, peak_kind = peaks()
@@ -264,6 +273,7 @@ def main():
                        "delta": "1/n", "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (CSR 137 MB; RR pool several GB per solve)"},
             "edge_visits_per_s": ev_all / (ms_max / 1000.0), "node_visits_per_s": nv_all / (ms_max / 1000.0),
+            "philox_draws_per_edge_visit": sum(r.draws for r in results) / max(1, ev),
             "rr_sets_per_solve": rr / args.steps, "rounds": [r.rounds for r in results],
             "kernel_ms": ks, "gpu_launches": launches, "clocks": clocks, "roofline": roof}
 

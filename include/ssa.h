@@ -157,6 +157,9 @@ typedef struct {
   int64_t cta_sets;          /* RR sets finished by the CTA-per-sample sampler tier */
   int64_t cta_edge_visits;   /* that tier's share of edge_visits */
   int64_t cta_node_visits;   /* that tier's share of node_visits */
+  int64_t cta_stored_entries; /* pool entries that tier wrote (hit-test sets store none) */
+  int64_t cta_stored_sets;   /* sets that tier wrote to the pool */
+  int64_t draws;             /* Philox draws: IC 4-edge groups that needed coins, LT picks */
   int64_t kernel_launches;   /* CUDA kernels this library launched for the solve */
   double seconds;            /* host wall time of the call */
   int32_t want_kstats;       /* in: 1 to time kernel classes with CUDA events */

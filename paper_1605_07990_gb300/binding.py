@@ -49,6 +49,7 @@ class ssa_result(C.Structure):
                 ("influence", C.c_double), ("rounds", C.c_int32), ("n_rr", C.c_int64),
                 ("pool_entries", C.c_int64), ("edge_visits", C.c_int64), ("node_visits", C.c_int64),
                 ("cta_sets", C.c_int64), ("cta_edge_visits", C.c_int64), ("cta_node_visits", C.c_int64),
+                ("cta_stored_entries", C.c_int64), ("cta_stored_sets", C.c_int64), ("draws", C.c_int64),
                 ("kernel_launches", C.c_int64), ("seconds", C.c_double), ("want_kstats", C.c_int32),
                 ("kstats", ssa_kstat * 5)]
 
@@ -180,6 +181,9 @@ class Result:
     cta_sets: int = 0
     cta_edge_visits: int = 0
     cta_node_visits: int = 0
+    cta_stored_entries: int = 0
+    cta_stored_sets: int = 0
+    draws: int = 0
     trace: list = field(default_factory=list)
     kstats: dict = field(default_factory=dict)
 
@@ -208,7 +212,8 @@ def _unpack(r, seeds, tr):
               "check_T": x.check_T, "stat": x.stat} for x in tr[:min(r.rounds, r.trace_cap)]]
     ks = {KERNEL_CLASSES[i]: {"launches": r.kstats[i].launches, "ms": r.kstats[i].ms} for i in range(5)}
     return Result(seeds.copy(), r.influence, r.rounds, r.n_rr, r.pool_entries, r.edge_visits, r.node_visits,
-                  r.kernel_launches, r.seconds, r.cta_sets, r.cta_edge_visits, r.cta_node_visits, trace, ks)
+                  r.kernel_launches, r.seconds, r.cta_sets, r.cta_edge_visits, r.cta_node_visits,
+                  r.cta_stored_entries, r.cta_stored_sets, r.draws, trace, ks)
 
 
 def ssa_solve(g: Graph, algo, model, k, eps, delta, seed, benefit=None, pool_bytes_cap=0, want_kstats=False,

@@ -219,8 +219,11 @@ struct Sampler {
   uint64_t wsum = 0;
   int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
   int64_t cta_edge_visits = 0, cta_node_visits = 0, cta_samples = 0;
+  int64_t cta_store_nodes = 0, cta_store_sets = 0;  // the CTA tier's sets written to the pool
+  int64_t draws = 0;  // Philox draws of IC edge groups / LT picks
 
   void tally(int64_t count) {
+    draws += (int64_t)h_ctr->draws;
     edge_visits += (int64_t)h_ctr->edge_visits;
     node_visits += (int64_t)h_ctr->node_visits;
     cta_edge_visits += (int64_t)h_ctr->cta_edge_visits;
@@ -318,9 +321,10 @@ struct Sampler {
   // no finished set is sampled twice.
   ssa_status append(DevPool& P, uint64_t seed, uint32_t stream, int64_t count, Exec& X) {
     if (count <= 0) return SSA_OK;
-    if (P.count == 0 && count > 4096) {
-      TRY(append(P, seed, stream, 1024, X));
-      count -= 1024;
+    if (P.count == 0 && count > 1024) {
+      const int64_t pilot = std::min<int64_t>(512, count / 4);
+      TRY(append(P, seed, stream, pilot, X));
+      count -= pilot;
     }
     const int64_t j0 = P.count;
     if (j0 + count > (int64_t)0x7FFFFFFF) return fail(SSA_E_POOL_FULL, "more than 2^31 RR sets");
@@ -354,6 +358,7 @@ struct Sampler {
       TRY(run(J, X, cursor0));
       ev += h_ctr->edge_visits;
       nv += h_ctr->node_visits;
+      draws += (int64_t)h_ctr->draws;
       cev += h_ctr->cta_edge_visits;
       cnv += h_ctr->cta_node_visits;
       csets += h_ctr->big_count;
@@ -377,7 +382,9 @@ struct Sampler {
     node_visits += (int64_t)nv;
     cta_edge_visits += (int64_t)cev;
     cta_node_visits += (int64_t)cnv;
+    cta_store_nodes += (int64_t)cnv;
     cta_samples += (int64_t)csets;
+    cta_store_sets += (int64_t)csets;
     samples += count;
     P.entries = (int64_t)cursor0;
     P.count = j0 + count;
@@ -567,6 +574,27 @@ struct Cover {
   }
 };
 
+// Cov of the seeds over the fresh sets [j0, j0+count) of `stream`, sampled in
+// hit-test mode (each sample stops at its first seed).
+ssa_status stare_hits(Sampler& S, Cover& C, uint64_t seed, uint32_t stream, int64_t j0, int64_t count,
+                      const int32_t* d_seeds, int k, int64_t* cov, Exec& X) {
+  const int64_t words = (S.g.n + 31) / 32;
+  CU(cudaMemsetAsync(S.seed_bits, 0, sizeof(uint32_t) * (size_t)words, X.st));
+  CU(launch_set_bits(d_seeds, k, S.seed_bits, nullptr, X.st));
+  X.launches += 1;
+  TRY(S.hits(seed, stream, j0, count, X));
+  int h = X.begin(SSA_K_STARE);
+  CU(cudaMemsetAsync(C.d_count, 0, sizeof(unsigned long long), X.st));
+  CU(launch_count_flags(S.hit, count, C.d_count, X.st, X.num_sms));
+  X.end(h);
+  X.launches += 1;
+  unsigned long long c = 0;
+  CU(cudaMemcpyAsync(&c, C.d_count, sizeof(c), cudaMemcpyDeviceToHost, X.st));
+  CU(cudaStreamSynchronize(X.st));
+  *cov = (int64_t)c;
+  return SSA_OK;
+}
+
 // Estimate-Inf (Algorithm 3) on the device: hit-test batches of fresh sets
 // of `stream`, then the first T whose prefix of successes reaches `need`.
 ssa_status estimate_inf_dev(Sampler& S, Cover& C, uint64_t seed, uint32_t stream, const int32_t* d_seeds, int k,
@@ -735,11 +763,14 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
           }
         }
       } else {
+        // R_t = samples [0, N) are in the pool; the check half R^c_t = [N, 2N)
+        // only needs "does S meet R_j" now, so it is sampled in hit-test mode
+        // (early exit) and stored afterwards only if the loop goes on, when
+        // it becomes the second half of R_{t+1} (same keys, same sets).
         if (t == 1 && (st = S.append(pool, p->seed, 0, N, X)) != SSA_OK) break;
-        if ((st = S.append(pool, p->seed, 0, 2 * N - pool.count, X)) != SSA_OK) break;
         int64_t cov = 0, c = 0;
         if ((st = C.greedy(pool, N, k, seeds.data(), gains.data(), &cov, X)) != SSA_OK) break;
-        if ((st = C.coverage_range(pool, N, 2 * N, &c, X)) != SSA_OK) break;
+        if ((st = stare_hits(S, C, p->seed, 0, N, N, C.d_seeds, k, &c, X)) != SSA_OK) break;
         rec.cov = cov;
         rec.check_cov = c;
         influence = (double)cov * scale / (double)N;
@@ -759,6 +790,13 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
       if (!stop && ((double)N >= P.n_max || t >= P.i_max)) stop = 2;  // sample cap
       rec.stop = stop ? 1 : 0;
       if (out->trace && t <= out->trace_cap) out->trace[t - 1] = rec;
+      if (dssa) {
+        if (stop) {
+          extra_rr += N;  // R^c_t was drawn (hit-tested) but not stored
+        } else if ((st = S.append(pool, p->seed, 0, N, X)) != SSA_OK) {
+          break;
+        }
+      }
       if (stop) break;
     }
   } while (false);
@@ -774,6 +812,9 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     out->cta_sets = S.cta_samples;
     out->cta_edge_visits = S.cta_edge_visits;
     out->cta_node_visits = S.cta_node_visits;
+    out->cta_stored_entries = S.cta_store_nodes;
+    out->cta_stored_sets = S.cta_store_sets;
+    out->draws = S.draws;
     out->kernel_launches = X.launches;
     X.collect(out->kstats);
   } else {

@@ -28,6 +28,7 @@ struct Counters {
   unsigned long long node_visits;  // nodes added to RR sets
   unsigned long long cta_edge_visits;  // the CTA tier's share of the two above
   unsigned long long cta_node_visits;
+  unsigned long long draws;        // Philox draws (IC: one per 4-edge group that needed coins)
   unsigned long long ok_end;        // end of the last pool reservation that fit
   unsigned long long fail_count;    // samples whose reservation did not fit (listed in fail_list)
   unsigned int pool_overflow;      // a reservation passed pool_cap

@@ -98,8 +98,8 @@ __device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u) {
 // may report nodes already in the set so their edges need no draw.
 template <class Known, class Visit>
 __device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
-                                          int lane, uint32_t* stage, unsigned long long& ev, Known&& known,
-                                          Visit&& visit) {
+                                          int lane, uint32_t* stage, unsigned long long& ev,
+                                          unsigned long long& draws, Known&& known, Visit&& visit) {
   uint32_t lo = 0, hi = 0;  // edge positions fit 32 bits (m < 2^31)
   if (v >= 0) {
     lo = (uint32_t)__ldg(g.off + v);
@@ -139,6 +139,7 @@ __device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const u
       if ((need & 4u) && known(u2)) need &= ~4u;
       if ((need & 8u) && known(u3)) need &= ~8u;
       if (need) {
+        ++draws;
         const uint4 r = philox_x(grp, sc, rk);
         if ((need & 1u) && edge_live(r.x, A.y)) cand |= 1u;
         if ((need & 2u) && edge_live(r.y, A.w)) cand |= 2u;
@@ -148,6 +149,12 @@ __device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const u
     }
     const unsigned any = __ballot_sync(FULL_MASK, cand != 0u);
     if (!any) continue;
+    if (!__any_sync(FULL_MASK, (cand & (cand - 1u)) != 0u)) {
+      // at most one candidate per lane (the common case): no staging
+      const uint32_t u = !cand ? NO_NODE : (cand & 1u) ? u0 : (cand & 2u) ? u1 : (cand & 4u) ? u2 : u3;
+      if (visit(u, lt_mask)) return true;
+      continue;
+    }
     const int c = __popc(cand);
     const int cin = warp_inclusive_scan(c, lane);
     const int ctot = __shfl_sync(FULL_MASK, cin, 31);
@@ -168,11 +175,13 @@ __device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const u
   return false;
 }
 
-__device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev, unsigned long long nv, int lane,
-                                            bool cta_tier) {
+__device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev, unsigned long long nv,
+                                            unsigned long long dr, int lane, bool cta_tier) {
   ev = warp_sum(ev);
   nv = warp_sum(nv);
+  dr = warp_sum(dr);
   if (lane == 0) {
+    if (dr) atomicAdd(&ctr->draws, dr);
     if (ev) atomicAdd(&ctr->edge_visits, ev);
     if (nv) atomicAdd(&ctr->node_visits, nv);
     if (cta_tier && ev) atomicAdd(&ctr->cta_edge_visits, ev);
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
   uint4* H4 = reinterpret_cast<uint4*>(H);
   for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
   __syncwarp();
-  unsigned long long ev = 0, nv = 0;
+  unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, known, visit);
+      expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, known, visit);
       head += cnt;
     }
     __syncwarp();
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
     for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
     __syncwarp();
   }
-  flush_stats(J.ctr, ev, nv, lane, false);
+  flush_stats(J.ctr, ev, nv, dr, lane, false);
 }
 
 // LT live-edge walk (one keyed in-neighbour per node), warp per sample: every
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
   __shared__ int32_t s_q[WT_WARPS][LT_QCAP];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* Q = s_q[wid];
-  unsigned long long ev = 0, nv = 0;
+  unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
@@ -311,7 +320,10 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
       if (d == 0) break;
       const uint4 r = philox_x((uint32_t)cur, sc, J.rk);
       const int32_t u = (int32_t)__ldg(&J.g.edge[lo + __umulhi(r.x, (uint32_t)d)].x);
-      if (lane == 0) ev += 1;
+      if (lane == 0) {
+        ev += 1;
+        dr += 1;
+      }
       bool found = false;
       for (int i = lane; i < tail; i += 32) found |= (Q[i] == u);
       if (__any_sync(FULL_MASK, found)) break;
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
     }
     __syncwarp();
   }
-  flush_stats(J.ctr, ev, nv, lane, false);
+  flush_stats(J.ctr, ev, nv, dr, lane, false);
 }
 
 // CTA tier: one CTA per large sample.
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
   if (SMEM_BITMAP)
     for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
   const long long big_count = (long long)*((volatile unsigned long long*)&J.ctr->big_count);
-  unsigned long long ev = 0, nv = 0;
+  unsigned long long ev = 0, nv = 0, dr = 0;
   __syncthreads();
   for (;;) {
     if (tid == 0) s_item = (long long)atomicAdd(&J.ctr->big_work, 1ull);
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
           if (b >= lvl_end) break;
           const int cnt = min(32, lvl_end - b);
           const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
-          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, known, visit)) break;
+          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, dr, known, visit)) break;
         }
         __syncthreads();
         lvl_begin = lvl_end;
@@ -427,6 +439,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
         const uint4 r = philox_x((uint32_t)cur, sc, J.rk);
         const int32_t u = (int32_t)J.g.edge[lo + __umulhi(r.x, (uint32_t)(hi - lo))].x;
         ev += 1;
+        dr += 1;
         const uint32_t mask = 1u << (u & 31);
         if (bits[u >> 5] & mask) break;
         bits[u >> 5] |= mask;
@@ -469,7 +482,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
     }
     __syncthreads();
   }
-  flush_stats(J.ctr, ev, nv, lane, true);
+  flush_stats(J.ctr, ev, nv, dr, lane, true);
 }
 
 }  // namespace
