@@ -423,21 +423,34 @@ struct Sampler {
   }
 };
 
-// Node -> set index and greedy buffers.
+// Node -> set index and greedy buffers.  The pool only ever appends whole
+// batches, so the index is kept per batch: each batch is counted, scanned and
+// scattered once, its counts are added to a running total, and Max-Coverage
+// walks v*'s list in every batch.  A cut N inside a batch gets a temporary
+// filtered index for the partial batch.
 struct Cover {
+  struct Batch {
+    int64_t j0, j1;          // sample ids [j0, j1)
+    int64_t* off = nullptr;  // n+1
+    int32_t* samp = nullptr; // entries of the batch
+  };
   int64_t n = 0;
   int64_t n_pad = 0;
-  int32_t* cnt = nullptr;
-  int64_t* inv_off = nullptr;
+  std::vector<Batch> batches;
+  Batch partial_batch;       // temporary, for a cut inside a batch
+  int32_t* cnt_total = nullptr;  // counts of the cached batches
+  int32_t* cnt_tmp = nullptr;    // one batch's counts
+  int32_t* cnt = nullptr;        // working gains of the current Max-Coverage
   unsigned long long* cur = nullptr;
-  int32_t* inv_samp = nullptr;
-  int64_t inv_cap = 0;
   void* scan_tmp = nullptr;
   uint8_t* covered = nullptr;
   int64_t covered_cap = 0;
   uint8_t* in_seed = nullptr;
   unsigned long long* partial = nullptr;
-  int argmax_blocks = 0;
+  int partial_cap = 0;
+  unsigned int* sync = nullptr;
+  unsigned long long* chunk_q = nullptr;
+  int64_t chunk_cap = 0;
   int32_t* d_seeds = nullptr;
   int32_t* d_gains = nullptr;
   int k_cap = 0;
@@ -451,27 +464,39 @@ struct Cover {
   ssa_status init(int64_t nn, Exec& X) {
     n = nn;
     n_pad = (n + 3) & ~int64_t(3);
+    TRY(dev_alloc(&cnt_total, (size_t)n_pad, X.st));
+    TRY(dev_alloc(&cnt_tmp, (size_t)n_pad, X.st));
     TRY(dev_alloc(&cnt, (size_t)n_pad, X.st));
-    TRY(dev_alloc(&inv_off, (size_t)n + 1, X.st));
+    CU(cudaMemsetAsync(cnt_total, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
     TRY(dev_alloc(&cur, (size_t)n + 1, X.st));
     TRY(dev_alloc(&in_seed, (size_t)n_pad, X.st));
     CU(cudaMallocAsync(&scan_tmp, scan_tmp_bytes(n), X.st));
-    argmax_blocks = X.num_sms * 4;
-    TRY(dev_alloc(&partial, (size_t)argmax_blocks, X.st));
+    partial_cap = X.num_sms * 8;
+    TRY(dev_alloc(&partial, (size_t)partial_cap, X.st));
+    TRY(dev_alloc(&sync, 128, X.st));
     TRY(dev_alloc(&d_count, 1, X.st));
     TRY(dev_alloc(&d_first, 2, X.st));
     return SSA_OK;
   }
+  void free_batch(Batch& b, cudaStream_t st) {
+    dev_free(b.off, st);
+    dev_free(b.samp, st);
+  }
   void release(cudaStream_t st) {
+    for (auto& b : batches) free_batch(b, st);
+    batches.clear();
+    free_batch(partial_batch, st);
+    dev_free(cnt_total, st);
+    dev_free(cnt_tmp, st);
     dev_free(cnt, st);
-    dev_free(inv_off, st);
     dev_free(cur, st);
-    dev_free(inv_samp, st);
     if (scan_tmp) cudaFreeAsync(scan_tmp, st);
     scan_tmp = nullptr;
     dev_free(covered, st);
     dev_free(in_seed, st);
     dev_free(partial, st);
+    dev_free(sync, st);
+    dev_free(chunk_q, st);
     dev_free(d_seeds, st);
     dev_free(d_gains, st);
     dev_free(d_count, st);
@@ -481,25 +506,59 @@ struct Cover {
     dev_free(hitc, st);
   }
 
-  // cnt / inv_off / inv_samp over the sets [0, N) of the pool
-  ssa_status build_index(const DevPool& P, int64_t N, Exec& X) {
-    int64_t e0, e1;
-    P.entry_range(0, N, &e0, &e1);
-    const bool exact = (e0 == 0) && [&] {
-      for (auto& b : P.bounds)
-        if (b.first == N) return true;
-      return false;
-    }();
-    TRY(dev_grow(&inv_samp, &inv_cap, std::max<int64_t>(e1, 1), 0, X.st));
-    int h = X.begin(SSA_K_INDEX);
-    CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
-    CU(launch_count_nodes(P.nodes, exact ? nullptr : P.samp, 0, e1, 0, N, cnt, X.st, X.num_sms));
+  // index of the samples [j0, j1) whose entries lie in [e0, e1); counts land in cnt_tmp
+  ssa_status index_range(const DevPool& P, int64_t j0, int64_t j1, int64_t e0, int64_t e1, bool filter, Batch& B,
+                         Exec& X) {
+    B.j0 = j0;
+    B.j1 = j1;
+    TRY(dev_alloc(&B.off, (size_t)n + 1, X.st));
+    TRY(dev_alloc(&B.samp, (size_t)std::max<int64_t>(e1 - e0, 1), X.st));
+    CU(cudaMemsetAsync(cnt_tmp, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
+    CU(launch_count_nodes(P.nodes, filter ? P.samp : nullptr, e0, e1, j0, j1, cnt_tmp, X.st, X.num_sms));
     int l = 0;
-    CU(launch_exclusive_scan(cnt, n, inv_off, scan_tmp, X.st, &l));
-    CU(cudaMemcpyAsync(cur, inv_off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, X.st));
-    CU(launch_scatter_index(P.nodes, P.samp, 0, e1, 0, N, cur, inv_samp, X.st, X.num_sms));
-    X.end(h);
+    CU(launch_exclusive_scan(cnt_tmp, n, B.off, scan_tmp, X.st, &l));
+    // positions inside the batch's own sample array: offsets start at 0
+    CU(cudaMemcpyAsync(cur, B.off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, X.st));
+    CU(launch_scatter_index(P.nodes, P.samp, e0, e1, j0, j1, cur, B.samp, X.st, X.num_sms));
     X.launches += 2 + l;
+    return SSA_OK;
+  }
+
+  // Make the index cover the sets [0, N): cached whole batches plus, for a
+  // cut inside a batch, a temporary partial one.  Leaves the counts of [0, N)
+  // in `cnt`.
+  ssa_status build_index(const DevPool& P, int64_t N, Exec& X) {
+    int h = X.begin(SSA_K_INDEX);
+    free_batch(partial_batch, X.st);
+    if (!batches.empty() && batches.back().j1 > N) {
+      // a smaller cut than before (direct callers): start the cache over
+      for (auto& b : batches) free_batch(b, X.st);
+      batches.clear();
+      CU(cudaMemsetAsync(cnt_total, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
+    }
+    // cache every whole pool batch below N that is not indexed yet
+    for (size_t i = 1; i < P.bounds.size(); ++i) {
+      const int64_t j0 = P.bounds[i - 1].first, j1 = P.bounds[i].first;
+      if (j1 > N) break;
+      if (!batches.empty() && batches.back().j1 >= j1) continue;
+      if (batches.size() >= (size_t)GREEDY_MAX_LISTS - 1)
+        return fail(SSA_E_INTERNAL, "more than %d index batches", GREEDY_MAX_LISTS - 1);
+      Batch B;
+      TRY(index_range(P, j0, j1, P.bounds[i - 1].second, P.bounds[i].second, false, B, X));
+      CU(launch_add_counts(cnt_total, cnt_tmp, n, X.st, X.num_sms));
+      X.launches += 1;
+      batches.push_back(B);
+    }
+    CU(cudaMemcpyAsync(cnt, cnt_total, sizeof(int32_t) * (size_t)n_pad, cudaMemcpyDeviceToDevice, X.st));
+    const int64_t covered_to = batches.empty() ? 0 : batches.back().j1;
+    if (covered_to < N) {
+      int64_t e0, e1;
+      P.entry_range(covered_to, N, &e0, &e1);
+      TRY(index_range(P, covered_to, N, e0, e1, true, partial_batch, X));
+      CU(launch_add_counts(cnt, cnt_tmp, n, X.st, X.num_sms));
+      X.launches += 1;
+    }
+    X.end(h);
     return SSA_OK;
   }
 
@@ -514,32 +573,46 @@ struct Cover {
       k_cap = k;
     }
     TRY(dev_grow(&covered, &covered_cap, std::max<int64_t>(N, 1), 0, X.st));
+    {
+      // queued decrement chunks of one pick: at most one per 2048 entries of [0, N)
+      int64_t e0 = 0, e1 = 0;
+      P.entry_range(0, N, &e0, &e1);
+      TRY(dev_grow(&chunk_q, &chunk_cap, e1 / 2048 + 1, 0, X.st));
+    }
     int h = X.begin(SSA_K_GREEDY);
     CU(cudaMemsetAsync(covered, 0, (size_t)std::max<int64_t>(N, 1), X.st));
-    CU(cudaMemsetAsync(in_seed, 0, (size_t)n_pad, X.st));
+    CU(cudaMemsetAsync(sync, 0, sizeof(unsigned int) * 128, X.st));
     // padding nodes can never be picked
-    if (n_pad > n) CU(cudaMemsetAsync(in_seed + n, 1, (size_t)(n_pad - n), X.st));
-    GreedyBufs b;
-    b.cnt = cnt;
-    b.inv_off = inv_off;
-    b.inv_samp = inv_samp;
-    b.pool_nodes = P.nodes;
-    b.set_start = P.set_start;
-    b.set_len = P.set_len;
-    b.covered = covered;
-    b.in_seed = in_seed;
-    b.partial = partial;
-    b.seeds = d_seeds;
-    b.gains = d_gains;
-    b.n = n;
-    b.argmax_blocks = argmax_blocks;
-    for (int i = 0; i < k; ++i) CU(launch_greedy_step(b, i, X.st, X.num_sms));
+    if (n_pad > n) CU(cudaMemsetAsync(cnt + n, 0xC0, sizeof(int32_t) * (size_t)(n_pad - n), X.st));
+    GreedyJob J{};
+    J.cnt = cnt;
+    J.n_pad = n_pad;
+    J.nlists = 0;
+    for (auto& b : batches) J.lists[J.nlists++] = InvList{b.off, b.samp};
+    if (partial_batch.off) J.lists[J.nlists++] = InvList{partial_batch.off, partial_batch.samp};
+    J.pool_nodes = P.nodes;
+    J.set_start = P.set_start;
+    J.set_len = P.set_len;
+    J.covered = covered;
+    J.seeds = d_seeds;
+    J.gains = d_gains;
+    J.k = k;
+    J.partial = partial;
+    J.partial_cap = partial_cap;
+    J.sync = sync;
+    J.chunk_q = chunk_q;
+    J.chunk_cap = chunk_cap;
+    int blocks = 0;
+    CU(launch_greedy(J, X.st, X.num_sms, &blocks));
     X.end(h);
-    X.launches += 2 * k;
+    X.launches += 1;
     std::vector<int32_t> g32((size_t)k);
+    unsigned int hsync[128] = {};
     CU(cudaMemcpyAsync(seeds, d_seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
     CU(cudaMemcpyAsync(g32.data(), d_gains, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
+    CU(cudaMemcpyAsync(hsync, sync, sizeof(hsync), cudaMemcpyDeviceToHost, X.st));
     CU(cudaStreamSynchronize(X.st));
+    if (hsync[64]) return fail(SSA_E_TIMEOUT, "greedy grid barrier timed out");
     int64_t c = 0;
     for (int i = 0; i < k; ++i) {
       gains[i] = g32[(size_t)i];

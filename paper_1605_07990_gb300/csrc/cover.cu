@@ -117,9 +117,6 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int32_t* in, int64_t n
 }
 
 // ---- greedy ----
-__device__ __forceinline__ unsigned long long gain_key(int32_t c, uint8_t taken, uint32_t v) {
-  return taken ? 0ull : (((unsigned long long)(uint32_t)(c + 1)) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
-}
 
 __device__ __forceinline__ unsigned long long block_max(unsigned long long x, unsigned long long* s) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -145,59 +142,147 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
   return x;
 }
 
-__global__ void __launch_bounds__(TPB) k_argmax(const int32_t* __restrict__ cnt, const uint8_t* __restrict__ in_seed,
-                                                int64_t n, unsigned long long* partial) {
-  __shared__ unsigned long long s[32];
-  unsigned long long best = 0;
-  const int64_t n4 = n >> 2;
-  const int4* c4 = reinterpret_cast<const int4*>(cnt);
-  const uchar4* s4 = reinterpret_cast<const uchar4*>(in_seed);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    const int4 c = __ldg(c4 + i);
-    const uchar4 t = __ldg(s4 + i);
-    const uint32_t v = (uint32_t)(i * 4);
-    unsigned long long k;
-    k = gain_key(c.x, t.x, v);     best = k > best ? k : best;
-    k = gain_key(c.y, t.y, v + 1); best = k > best ? k : best;
-    k = gain_key(c.z, t.z, v + 2); best = k > best ? k : best;
-    k = gain_key(c.w, t.w, v + 3); best = k > best ? k : best;
+// Persistent greedy: all k picks of Algorithm 2 in one cooperative launch.
+// Per pick: every block scans its slice of the gains for the packed max key
+// (largest gain, then smallest id; picked nodes hold a negative gain), a grid
+// barrier, every block reduces the per-block partials to the same (v*, gain),
+// then warps walk v*'s inverted lists of all index batches and, for each
+// newly covered set, decrement the gains of its members; a second barrier
+// closes the pick.  Barrier waits are bounded: on a timeout the kernel sets
+// sync[2] and every block returns.
+// sync layout: arrival count, generation and timeout flag on separate
+// 128-byte lines so that polling does not contend with the arrivals.
+constexpr int SYNC_COUNT = 0, SYNC_GEN = 32, SYNC_ERR = 64, SYNC_CHUNKS = 96, SYNC_WORDS = 128;
+constexpr int DEC_CHUNK = 2048;  // covered sets longer than this are decremented in chunks by all warps
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* sync) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = sync + SYNC_GEN;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(sync + SYNC_COUNT, 1u) + 1u == gridDim.x) {
+      atomicExch(sync + SYNC_COUNT, 0u);
+      __threadfence();
+      atomicAdd(sync + SYNC_GEN, 1u);
+    } else {
+      unsigned int ns = 8;
+      for (long long spins = 0; *gen == g; ++spins) {
+        if (spins > (1ll << 22)) {  // seconds: a barrier never takes that long
+          atomicExch(sync + SYNC_ERR, 1u);
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+      }
+    }
+    __threadfence();
   }
-  for (int64_t v = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long k = gain_key(cnt[v], in_seed[v], (uint32_t)v);
-    best = k > best ? k : best;
-  }
-  best = block_max(best, s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = best;
+  __syncthreads();
+  return *((volatile unsigned int*)(sync + SYNC_ERR)) == 0u;
 }
 
-__global__ void __launch_bounds__(TPB) k_cover(GreedyBufs b, int step) {
-  __shared__ unsigned long long s[32];
-  unsigned long long best = 0;
-  for (int i = threadIdx.x; i < b.argmax_blocks; i += blockDim.x) {
-    const unsigned long long k = b.partial[i];
-    best = k > best ? k : best;
+__device__ __forceinline__ unsigned long long gain_key(int32_t c, uint32_t v) {
+  return c < 0 ? 0ull : (((unsigned long long)(uint32_t)(c + 1)) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
+}
+
+// gains of the `len` members at mem lose one each (a warp, lanes striped)
+__device__ __forceinline__ void decrement_members(int32_t* cnt, const int32_t* mem, int32_t len, int lane) {
+  int t = lane;
+  for (; t + 96 < len; t += 128) {  // four independent loads in flight per lane
+    const int32_t a = __ldg(mem + t), b = __ldg(mem + t + 32), c = __ldg(mem + t + 64), d = __ldg(mem + t + 96);
+    atomicSub(cnt + a, 1);
+    atomicSub(cnt + b, 1);
+    atomicSub(cnt + c, 1);
+    atomicSub(cnt + d, 1);
   }
-  best = block_max(best, s);
-  const int32_t vstar = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    b.seeds[step] = vstar;
-    b.gains[step] = (int32_t)((uint32_t)(best >> 32) - 1u);
-    b.in_seed[vstar] = 1;
-  }
-  const int64_t q0 = b.inv_off[vstar], q1 = b.inv_off[vstar + 1];
+  for (; t < len; t += 32) atomicSub(cnt + __ldg(mem + t), 1);
+}
+
+__global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
+  __shared__ unsigned long long s_red[32];
+  __shared__ int64_t s_lo[GREEDY_MAX_LISTS], s_hi[GREEDY_MAX_LISTS];
   const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t q = q0 + warp; q < q1; q += nwarps) {
-    const int32_t j = b.inv_samp[q];
-    if (b.covered[j]) continue;
-    __syncwarp();
-    if (lane == 0) b.covered[j] = 1;
-    const int64_t st = b.set_start[j];
-    const int32_t len = b.set_len[j];
-    for (int i = lane; i < len; i += 32) atomicSub(b.cnt + b.pool_nodes[st + i], 1);
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t warp = gtid >> 5, nwarps = gthreads >> 5;
+  const int64_t n4 = J.n_pad >> 2;
+  const int4* c4 = reinterpret_cast<const int4*>(J.cnt);
+  for (int i = 0; i < J.k; ++i) {
+    unsigned long long best = 0;
+    for (int64_t q = gtid; q < n4; q += gthreads) {
+      const int4 c = __ldcg(c4 + q);
+      const uint32_t v = (uint32_t)(q * 4);
+      unsigned long long key;
+      key = gain_key(c.x, v);     best = key > best ? key : best;
+      key = gain_key(c.y, v + 1); best = key > best ? key : best;
+      key = gain_key(c.z, v + 2); best = key > best ? key : best;
+      key = gain_key(c.w, v + 3); best = key > best ? key : best;
+    }
+    best = block_max(best, s_red);
+    if (threadIdx.x == 0) J.partial[blockIdx.x] = best;
+    if (!grid_barrier(J.sync)) return;
+    best = 0;
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
+      const unsigned long long key = __ldcg(J.partial + t);
+      best = key > best ? key : best;
+    }
+    best = block_max(best, s_red);
+    const int32_t vstar = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
+    if (threadIdx.x < J.nlists) {
+      s_lo[threadIdx.x] = J.lists[threadIdx.x].off[vstar];
+      s_hi[threadIdx.x] = J.lists[threadIdx.x].off[vstar + 1];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      J.seeds[i] = vstar;
+      J.gains[i] = (int32_t)((uint32_t)(best >> 32) - 1u);
+    }
+    __syncthreads();
+    unsigned int* chunks = J.sync + SYNC_CHUNKS + (i & 1) * 16;
+    for (int b = 0; b < J.nlists; ++b) {
+      const int32_t* samp = J.lists[b].samp;
+      for (int64_t q = s_lo[b] + warp; q < s_hi[b]; q += nwarps) {
+        const int32_t j = samp[q];
+        if (__ldcg(J.covered + j)) continue;
+        __syncwarp();
+        if (lane == 0) J.covered[j] = 1;
+        const int32_t len = J.set_len[j];
+        int32_t mine = len;
+        if (len > DEC_CHUNK) {
+          // keep the first chunk, queue the rest for every warp after the barrier
+          mine = DEC_CHUNK;
+          const int nq = (len - 1) / DEC_CHUNK;
+          unsigned int at = 0;
+          if (lane == 0) at = atomicAdd(chunks, (unsigned int)nq);
+          at = __shfl_sync(FULL_MASK, at, 0);
+          for (int c = lane; c < nq; c += 32)
+            J.chunk_q[at + c] = ((unsigned long long)(uint32_t)j << 32) | (uint32_t)((c + 1) * DEC_CHUNK);
+        }
+        decrement_members(J.cnt, J.pool_nodes + J.set_start[j], mine, lane);
+      }
+    }
+    // v* leaves the candidates for good (its remaining decrements keep it negative)
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(J.cnt + vstar, INT32_MIN / 2);
+    if (!grid_barrier(J.sync)) return;
+    // the other parity's queue was drained in the previous pick: reset it for the next one
+    if (blockIdx.x == 0 && threadIdx.x == 0) J.sync[SYNC_CHUNKS + ((i + 1) & 1) * 16] = 0u;
+    const unsigned int nchunks = *(volatile unsigned int*)chunks;
+    if (nchunks > 0) {
+      for (int64_t c = warp; c < (int64_t)nchunks; c += nwarps) {
+        const unsigned long long e = J.chunk_q[c];
+        const int32_t j = (int32_t)(e >> 32), from = (int32_t)(uint32_t)e;
+        const int32_t len = J.set_len[j];
+        const int32_t cnt = min(DEC_CHUNK, len - from);
+        decrement_members(J.cnt, J.pool_nodes + J.set_start[j] + from, cnt, lane);
+      }
+      if (!grid_barrier(J.sync)) return;
+    }
   }
+}
+
+__global__ void k_add_counts(int32_t* __restrict__ total, const int32_t* __restrict__ add, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    total[i] += add[i];
 }
 
 // ---- stare ----
@@ -349,9 +434,22 @@ cudaError_t launch_scatter_index(const int32_t* nodes, const int32_t* samp, int6
   return cudaGetLastError();
 }
 
-cudaError_t launch_greedy_step(const GreedyBufs& b, int step, cudaStream_t st, int num_sms) {
-  k_argmax<<<b.argmax_blocks, TPB, 0, st>>>(b.cnt, b.in_seed, b.n, b.partial);
-  k_cover<<<num_sms * 4, TPB, 0, st>>>(b, step);
+cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used) {
+  // one 1024-thread block per SM: the fewest barrier arrivals with a full machine
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy, 1024, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int blocks = num_sms;
+  if (blocks > J.partial_cap) return cudaErrorInvalidValue;
+  *blocks_used = blocks;
+  GreedyJob j = J;
+  void* args[] = {&j};
+  return cudaLaunchCooperativeKernel((const void*)k_greedy, dim3(blocks), dim3(1024), args, 0, st);
+}
+
+cudaError_t launch_add_counts(int32_t* total, const int32_t* add, int64_t n, cudaStream_t st, int num_sms) {
+  k_add_counts<<<grid_stride_blocks(n, num_sms, 4), TPB, 0, st>>>(total, add, n);
   return cudaGetLastError();
 }
 

@@ -101,22 +101,33 @@ cudaError_t launch_scatter_index(const int32_t* nodes, const int32_t* samp, int6
                                  int64_t jhi, unsigned long long* cur, int32_t* inv_samp, cudaStream_t st,
                                  int num_sms);
 
-struct GreedyBufs {
-  int32_t* cnt;                 // n, working marginal gains
-  const int64_t* inv_off;       // n+1
-  const int32_t* inv_samp;      // entries
+constexpr int GREEDY_MAX_LISTS = 48;
+struct InvList {
+  const int64_t* off;           // n+1 offsets of one index batch
+  const int32_t* samp;          // its sample ids
+};
+struct GreedyJob {
+  int32_t* cnt;                 // n_pad working gains; negative = picked or padding
+  int64_t n_pad;                // multiple of 4
+  InvList lists[GREEDY_MAX_LISTS];
+  int nlists;
   const int32_t* pool_nodes;
   const int64_t* set_start;
   const int32_t* set_len;
-  uint8_t* covered;             // N
-  uint8_t* in_seed;             // n
-  unsigned long long* partial;  // argmax partials
+  uint8_t* covered;             // per sample id, zeroed
   int32_t* seeds;               // k (device)
   int32_t* gains;               // k (device)
-  int64_t n;
-  int argmax_blocks;
+  int k;
+  unsigned long long* partial;  // one per block
+  int partial_cap;
+  unsigned int* sync;           // 128 words, zeroed: count [0], generation [32], timeout flag [64],
+                                // chunk-queue lengths [96], [112]
+  unsigned long long* chunk_q;  // (set, first member) of queued decrement chunks
+  int64_t chunk_cap;
 };
-cudaError_t launch_greedy_step(const GreedyBufs& b, int step, cudaStream_t st, int num_sms);
+// All k picks in one cooperative launch (bounded grid barriers).
+cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used);
+cudaError_t launch_add_counts(int32_t* total, const int32_t* add, int64_t n, cudaStream_t st, int num_sms);
 
 cudaError_t launch_mark_hits(const int32_t* nodes, const int32_t* samp, int64_t e0, int64_t e1,
                              const uint8_t* in_seed, int64_t j0, int64_t j1, uint8_t* hit, cudaStream_t st,
