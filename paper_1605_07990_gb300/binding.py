@@ -304,6 +304,16 @@ class Pool:
         _check(lib().ssa_pool_export(self.h, int(first), int(count), _ptr(off), _ptr(nodes), int(cap)))
         return off, nodes[:off[-1]]
 
+    def set_sizes(self, first=0, count=None):
+        """|R_j| for j in [first, first+count) without copying the nodes."""
+        total = self.info()[0]
+        count = total - first if count is None else count
+        off = np.zeros(count + 1, dtype=np.int64)
+        st = lib().ssa_pool_export(self.h, int(first), int(count), _ptr(off), None, 0)
+        if st not in (SSA_OK, 1):  # SSA_E_ARG only reports the missing nodes buffer; off is filled
+            _check(st)
+        return np.diff(off)
+
     def sets(self, first=0, count=None, sort=True):
         off, nodes = self.export(first, count)
         out = [nodes[off[i]:off[i + 1]] for i in range(len(off) - 1)]

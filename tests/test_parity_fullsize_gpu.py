@@ -1,0 +1,101 @@
+"""GPU parity at the measured workloads' full sizes, in the launch
+configuration bench.py times (one solver, library-owned launch shapes).
+
+* D-SSA, LT, R-MAT 2^23 nodes / 2^27 draws, k=500, eps=0.05: the oracle
+  finishes the whole solve, so seeds, round trace and influence are compared
+  exactly.
+* D-SSA, trivalency IC, R-MAT 2^20 / 2^24, k=100, eps=0.1 (the bench
+  workload): the oracle needs ~50 ms per large RR set, so it checks sampled
+  sets one by one (small and large), and properties that hold at any size tie
+  the solve to the step entry points: the hit-test stare count equals Cov of
+  the stored check half, the solve's greedy equals ssa_max_coverage on the
+  same sets, and the oracle's membership test on sampled sets agrees with the
+  GPU hit flags."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+P = pytest.importorskip("paper_1605_07990_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def c2():
+    el = inputs.rmat(20, 1 << 24, seed=1)
+    og = oracle.Graph(el.n, el.src, el.dst, oracle.W_TRIVALENCY, None, 1)
+    gg = P.ssa_load_graph(el.n, el.src, el.dst, None, P.SSA_W_TRIVALENCY, 1)
+    yield el, og, gg
+    gg.free()
+
+
+def test_c3_full_solve_matches_oracle():
+    el = inputs.rmat(23, 1 << 27, seed=1)
+    og = oracle.Graph(el.n, el.src, el.dst, oracle.W_WC)
+    gg = P.ssa_load_graph(el.n, el.src, el.dst, None, P.SSA_W_WC)
+    n = el.n
+    g = P.Solver(gg).solve(P.SSA_ALGO_DSSA, P.SSA_LT, 500, 0.05, 1.0 / n, 1)
+    o = oracle.solve(og, oracle.DSSA, oracle.LT, 500, 0.05, 1.0 / n, 1)
+    assert np.array_equal(g.seeds, o.seeds)
+    assert g.trace == o.trace and g.rounds == o.rounds and g.n_rr == o.n_rr
+    assert g.influence == pytest.approx(o.influence, rel=1e-12, abs=0)
+    gg.free()
+
+
+def test_c2_sampled_rr_sets(c2):
+    el, og, gg = c2
+    N = 3731 * 32  # the bench solve's whole stream 0 (R_5 plus its check half)
+    pool = P.Pool(gg, P.SSA_IC, seed=1).grow(N)
+    rng = np.random.default_rng(7)
+    sizes = pool.set_sizes(0, N)
+    big = np.nonzero(sizes > 512)[0]
+    small = np.nonzero(sizes <= 512)[0]
+    picks = np.concatenate([rng.choice(big, 12, replace=False), rng.choice(small, 40, replace=False),
+                            [0, N - 1]])
+    for j in picks:
+        gset = np.sort(pool.sets(int(j), 1)[0])
+        oset = oracle.rr_set(og, oracle.IC, 1, 0, int(j))
+        assert np.array_equal(gset, oset), j
+    pool.free()
+
+
+def test_c2_solve_consistent_with_step_entry_points(c2):
+    el, og, gg = c2
+    n = el.n
+    s = P.Solver(gg)
+    r = s.solve(P.SSA_ALGO_DSSA, P.SSA_IC, 100, 0.1, 1.0 / n, 1)
+    last = r.trace[-1]
+    N = last["n_sets"]
+    pool = P.Pool(gg, P.SSA_IC, seed=1).grow(2 * N)
+    seeds, gains, cov = pool.max_coverage(N, 100)
+    assert np.array_equal(seeds, r.seeds) and cov == last["cov"]
+    # the solve sampled R^c_t in hit-test mode; Cov of the stored copy must agree
+    assert pool.coverage(N, N, r.seeds) == last["check_cov"]
+    assert r.n_rr == 2 * N and r.influence == cov * n / N
+    # oracle membership on sampled check-half sets agrees with the GPU sets
+    rng = np.random.default_rng(3)
+    S = set(int(x) for x in r.seeds)
+    for j in rng.choice(np.arange(N, 2 * N), 24, replace=False):
+        oset = oracle.rr_set(og, oracle.IC, 1, 0, int(j))
+        gset = np.sort(pool.sets(int(j), 1)[0])
+        assert np.array_equal(oset, gset)
+        hit = bool(S.intersection(oset.tolist()))
+        assert pool.coverage(int(j), 1, r.seeds) == int(hit)
+    pool.free()
+    s.free()
+
+
+def test_c2_estimate_inf_full_size(c2):
+    # SSA's stare step at the bench graph: hit-test batches and first-T search
+    el, og, gg = c2
+    S = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 64, 128], dtype=np.int32)
+    gT, gh = P.ssa_estimate_inf(gg, P.SSA_IC, 1, 3, S, 150.5, 4000)
+    oT, oh, _ = oracle.estimate_inf(og, oracle.IC, 1, 3, S, 150.5, 4000)
+    assert (gT, gh) == (oT, oh)
