@@ -156,6 +156,102 @@ def run_reference(args):
     return 0
 
 
+def serving_queries(nq, graphs_n, seed=7):
+    """c5 query mix: graph and model 50/50, k in {1,10,100,1000}, eps in {0.05,0.1,0.2},
+    delta = 1/n, seed = query index, every other query targeted (Zipf benefits)."""
+    import inputs
+    u = inputs.uniforms(6 * nq, seed).reshape(nq, 6)
+    qs = []
+    for i in range(nq):
+        g = int(u[i, 0] * 2)
+        qs.append({"graph": g, "model": int(u[i, 1] * 2), "k": [1, 10, 100, 1000][int(u[i, 2] * 4)],
+                   "eps": [0.05, 0.1, 0.2][int(u[i, 3] * 3)], "delta": 1.0 / graphs_n[g], "seed": i,
+                   "targeted": i % 2 == 1})
+    return qs
+
+
+def run_serving(args):
+    """Poisson stream of mixed queries against two resident graphs: the serving
+    loop (continuous admission, concurrent slots) against sequential solves."""
+    import torch
+    import __graft_entry__
+    import inputs
+    __graft_entry__.build()
+    import paper_1605_07990_gb300 as P
+    torch.cuda.set_device(0)
+    els = [inputs.rmat(20, 1 << 24, seed=1), inputs.rmat(23, 1 << 27, seed=1)]
+    gs = [P.ssa_load_graph(e.n, e.src, e.dst, None, P.SSA_W_WC) for e in els]
+    ws = [inputs.zipf_benefit(e.n, 1.2, seed=100 + i) for i, e in enumerate(els)]
+    qs = serving_queries(args.queries, [e.n for e in els])
+
+    def solve_seq(algo):
+        solvers = [P.Solver(g) for g in gs]
+        out, svc = [], []
+        for q in qs:
+            b = ws[q["graph"]] if q["targeted"] else None
+            t0 = time.perf_counter()
+            r = solvers[q["graph"]].solve(algo, q["model"], q["k"], q["eps"], q["delta"], q["seed"], benefit=b)
+            svc.append(time.perf_counter() - t0)
+            out.append(r)
+        for s_ in solvers:
+            s_.free()
+        return out, np.array(svc)
+
+    # warm-up: first solves pay for workspace allocation
+    for g, e in zip(gs, els):
+        P.ssa_solve(g, 1, 0, 10, 0.1, 1.0 / e.n, 12345)
+    seq_d, svc_d = solve_seq(P.SSA_ALGO_DSSA)
+    seq_s, svc_s = solve_seq(P.SSA_ALGO_SSA)
+    # Poisson arrivals at 0.8 of the sequential D-SSA capacity
+    rate = 0.8 / float(svc_d.mean())
+    arr = np.cumsum(-np.log1p(-inputs.uniforms(len(qs), 4242)) / rate)
+
+    def fifo(svc):
+        fin, lat = 0.0, []
+        for a, s_ in zip(arr, svc):
+            fin = max(a, fin) + s_
+            lat.append(fin - a)
+        lat = np.array(lat)
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "queries_per_s": len(qs) / fin, "saturated_queries_per_s": len(qs) / float(svc.sum())}
+
+    srv = P.Server(gs, slots=args.slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for q, a in zip(qs, arr):
+        delay = a - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        b = ws[q["graph"]] if q["targeted"] else None
+        tickets.append(srv.submit(q["graph"], P.SSA_ALGO_DSSA, q["model"], q["k"], q["eps"], q["delta"],
+                                  q["seed"], benefit=b))
+    live = [srv.wait(t) for t in tickets]
+    t_live = time.perf_counter() - t0
+    lat = np.array([r.latency_s for r in live])
+    same = sum(int(np.array_equal(x.seeds, y.seeds) and x.trace == y.trace) for x, y in zip(seq_d, live))
+    # saturated: everything at once
+    t1 = time.perf_counter()
+    tk = [srv.submit(q["graph"], P.SSA_ALGO_DSSA, q["model"], q["k"], q["eps"], q["delta"], q["seed"],
+                     benefit=ws[q["graph"]] if q["targeted"] else None) for q in qs]
+    sat = [srv.wait(t) for t in tk]
+    t_sat = time.perf_counter() - t1
+    srv.close()
+    line = {"metric": "serving queries/s and p50/p99 latency", "unit": "queries/s",
+            "value": len(qs) / t_live, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "c5 Poisson mix: R-MAT 2^20/2^24 and 2^23/2^27 (WC weights), IC/LT, "
+                                   "k in {1,10,100,1000}, eps in {0.05,0.1,0.2}, half targeted (Zipf 1.2)",
+                       "queries": len(qs), "arrival_rate_per_s": rate, "slots": args.slots},
+            "server": {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                       "queries_per_s": len(qs) / t_live, "saturated_queries_per_s": len(qs) / t_sat,
+                       "answers_equal_to_sequential": same},
+            "sequential_dssa": fifo(svc_d), "sequential_plain_ssa": fifo(svc_s),
+            "mean_service_ms": {"dssa": 1e3 * float(svc_d.mean()), "ssa": 1e3 * float(svc_s.mean())}}
+    print(json.dumps(line), flush=True)
+    for g in gs:
+        g.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,9 +265,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sample-only", type=int, default=0,
                     help="profiling case: only sample this many RR sets of the workload into a pool")
+    ap.add_argument("--serving", action="store_true", help="the Poisson serving mix instead of the solve bench")
+    ap.add_argument("--queries", type=int, default=2000)
+    ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
     import torch.distributed as dist

@@ -214,6 +214,43 @@ ssa_status ssa_estimate_inf(const ssa_graph* g, ssa_model model, uint64_t seed, 
                             int64_t t_max, int64_t* T, int64_t* hits);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous admission of queries against resident graphs.       */
+/* (The paper solves one query per run; its Sec. 6.3 TVM queries are WRIS   */
+/* solves, which ssa_params.benefit expresses.)                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct ssa_server ssa_server;
+
+typedef struct {
+  int64_t submitted, completed, failed, active, pending;
+  int64_t bytes_budget;      /* RR-pool byte budget shared by admitted requests */
+  int64_t bytes_in_use;      /* reserved by the requests now running */
+  double p50_ms, p99_ms;     /* submit-to-done latency of completed requests */
+} ssa_serve_stats;
+
+/* Start a server over n_graphs resident graphs (the handles must outlive the
+ * server) with `slots` worker slots (1..64), each with its own CUDA stream.
+ * pool_bytes: RR-pool budget shared by running requests (0 = 60% of free
+ * device memory).  A request is admitted FIFO when a slot is free and its
+ * estimated footprint (learned per graph, model and k range from finished
+ * requests) fits the budget, or when nothing else runs. */
+ssa_status ssa_server_create(const ssa_graph* const* graphs, int32_t n_graphs, int32_t slots, int64_t pool_bytes,
+                             ssa_server** out);
+/* Queue one solve (params and benefit array are copied).  *ticket names it. */
+ssa_status ssa_server_submit(ssa_server* s, int32_t graph, const ssa_params* p, uint64_t* ticket);
+/* If the request is done, copy its result (seeds: host int32[k]; out->trace
+ * may point to a host ssa_round buffer of out->trace_cap entries) and its
+ * submit-to-done latency in seconds, release the ticket and return its status;
+ * otherwise SSA_E_NOT_READY. */
+ssa_status ssa_server_poll(ssa_server* s, uint64_t ticket, int32_t* seeds, ssa_result* out, double* latency_s);
+/* As poll, but block up to timeout_s seconds (SSA_E_TIMEOUT if still running). */
+ssa_status ssa_server_wait(ssa_server* s, uint64_t ticket, double timeout_s, int32_t* seeds, ssa_result* out,
+                           double* latency_s);
+ssa_status ssa_server_stats(ssa_server* s, ssa_serve_stats* out);
+/* Finish the running requests, cancel the queued ones (SSA_E_CANCELLED), join. */
+ssa_status ssa_server_destroy(ssa_server* s);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free coverage count (no counterpart in the paper).            */
 /* ------------------------------------------------------------------------ */
 

@@ -54,6 +54,12 @@ class ssa_result(C.Structure):
                 ("kstats", ssa_kstat * 5)]
 
 
+class ssa_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("active", C.c_int64),
+                ("pending", C.c_int64), ("bytes_budget", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
 EXPORTS = {
     "ssa_status_str": (C.c_char_p, [C.c_int]),
     "ssa_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
@@ -78,6 +84,14 @@ EXPORTS = {
     "ssa_coverage": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p]),
     "ssa_estimate_inf": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
                                    C.c_int32, C.c_double, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ssa_server_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.POINTER(C.c_void_p)]),
+    "ssa_server_submit": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(ssa_params), C.POINTER(C.c_uint64)]),
+    "ssa_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(ssa_result),
+                                  C.POINTER(C.c_double)]),
+    "ssa_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.c_void_p, C.POINTER(ssa_result),
+                                  C.POINTER(C.c_double)]),
+    "ssa_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ssa_serve_stats)]),
+    "ssa_server_destroy": (C.c_int, [C.c_void_p]),
     "ssa_coverage_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
                                        C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
 }
@@ -370,3 +384,81 @@ def ssa_coverage_noalloc(n, nodes_ptr, samp_ptr, entries, first, count, seeds_pt
     _check(lib().ssa_coverage_noalloc(int(n), nodes_ptr, samp_ptr, int(entries), int(first), int(count),
                                       seeds_ptr, int(k), C.byref(cov), stream))
     return cov.value
+
+
+class Server:
+    """ssa_server*: continuous-admission serving loop over resident graphs."""
+
+    def __init__(self, graphs, slots=4, pool_bytes=0):
+        arr = (C.c_void_p * len(graphs))(*[g.h for g in graphs])
+        h = C.c_void_p()
+        _check(lib().ssa_server_create(arr, len(graphs), int(slots), int(pool_bytes), C.byref(h)))
+        self.h, self.graphs = h.value, list(graphs)
+        self._k = {}
+
+    def submit(self, graph, algo, model, k, eps, delta, seed, benefit=None):
+        b = None if benefit is None else np.ascontiguousarray(benefit, dtype=np.uint32)
+        p = _params(algo, model, k, eps, delta, seed, b, 0)
+        t = C.c_uint64()
+        _check(lib().ssa_server_submit(self.h, int(graph), C.byref(p), C.byref(t)))
+        self._k[t.value] = int(k)
+        return t.value
+
+    def _take(self, fn, ticket, *extra):
+        k = self._k.get(ticket, 1)  # unknown tickets are reported by the library
+        r, seeds, tr = _result(k, 64, False)
+        lat = C.c_double()
+        st = fn(self.h, C.c_uint64(ticket), *extra, seeds.ctypes.data, C.byref(r), C.byref(lat))
+        if st == 8:  # SSA_E_NOT_READY
+            return None
+        self._k.pop(ticket, None)
+        _check(st)
+        out = _unpack(r, seeds, tr)
+        out.latency_s = lat.value
+        return out
+
+    def poll(self, ticket):
+        return self._take(lib().ssa_server_poll, ticket)
+
+    def wait(self, ticket, timeout_s=600.0):
+        return self._take(lib().ssa_server_wait, ticket, C.c_double(timeout_s))
+
+    def stats(self):
+        st = ssa_serve_stats()
+        _check(lib().ssa_server_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self.h:
+            _check(lib().ssa_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ssa_server_create(graphs, slots=4, pool_bytes=0) -> Server:
+    return Server(graphs, slots, pool_bytes)
+
+
+def ssa_server_submit(s: Server, graph, *a, **kw):
+    return s.submit(graph, *a, **kw)
+
+
+def ssa_server_poll(s: Server, ticket):
+    return s.poll(ticket)
+
+
+def ssa_server_wait(s: Server, ticket, timeout_s=600.0):
+    return s.wait(ticket, timeout_s)
+
+
+def ssa_server_stats(s: Server):
+    return s.stats()
+
+
+def ssa_server_destroy(s: Server):
+    s.close()

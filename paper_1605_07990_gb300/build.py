@@ -19,7 +19,7 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",
           "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["sample.cu", "cover.cu", "graph.cu", "noalloc.cu", "api.cpp"]
+SOURCES = ["sample.cu", "cover.cu", "graph.cu", "noalloc.cu", "api.cpp", "serve.cpp"]
 
 
 def _stale(out: str, deps) -> bool:

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <chrono>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -603,6 +604,10 @@ struct Cover {
     J.chunk_q = chunk_q;
     J.chunk_cap = chunk_cap;
     int blocks = 0;
+    // one cooperative greedy grid on the device at a time (solvers on other
+    // host threads, e.g. serving slots, wait here)
+    static std::mutex coop_mu;
+    std::lock_guard<std::mutex> coop_lock(coop_mu);
     CU(launch_greedy(J, X.st, X.num_sms, &blocks));
     X.end(h);
     X.launches += 1;
@@ -1036,9 +1041,22 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
   return SSA_OK;
 }
 
+ssa_solver* new_solver_keep_pool_memory() {
+  // Solves allocate and free multi-GB workspaces stream-ordered; keep freed
+  // memory in the device's default pool instead of unmapping it at each sync.
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  return new ssa_solver();
+}
+
 ssa_status ssa_solver_create(const ssa_graph* g, void* stream, int64_t pool_bytes_cap, ssa_solver** out) {
   if (!g || !out) return fail(SSA_E_ARG, "null graph or output");
-  ssa_solver* s = new ssa_solver();
+  ssa_solver* s = new_solver_keep_pool_memory();
   s->g = g;
   cudaGetDevice(&s->device);
   if (stream) {
