@@ -96,6 +96,9 @@ struct ssa_graph {
   int64_t* off = nullptr;
   uint2* edge = nullptr;
   int64_t bytes = 0;
+  // IC sampler hand-over size chosen by the autotuner (-1: not tuned yet)
+  mutable std::mutex tune_mu;
+  mutable int tuned_mid_cap = -1;
   GraphView view() const {
     GraphView v;
     v.n = n;
@@ -208,6 +211,11 @@ struct Sampler {
   Counters* h_ctr = nullptr;  // pinned
   int64_t* big_list = nullptr;
   int64_t big_cap = 0;
+  int64_t* mid_list = nullptr;
+  int64_t mid_list_cap = 0;
+  uint32_t* mid_hash = nullptr;
+  int32_t* mid_queue = nullptr;
+  uint32_t* mid_slots = nullptr;
   int64_t* fail_list = nullptr;  // samples whose pool reservation did not fit
   int64_t* redo_list = nullptr;  // the previous attempt's fail list, re-run
   int64_t fail_cap = 0, redo_cap = 0;
@@ -218,6 +226,7 @@ struct Sampler {
   uint32_t* seed_bits = nullptr;
   uint64_t* bprefix = nullptr;
   uint64_t wsum = 0;
+  int mid_cap = 16384;  // IC: largest set the global warp tier keeps (0 = none)
   int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
   int64_t cta_edge_visits = 0, cta_node_visits = 0, cta_samples = 0;
   int64_t cta_store_nodes = 0, cta_store_sets = 0;  // the CTA tier's sets written to the pool
@@ -236,6 +245,10 @@ struct Sampler {
   ssa_status init(const ssa_graph* G, int mdl, const uint32_t* benefit, Exec& X) {
     g = G->view();
     model = mdl;
+    {
+      std::lock_guard<std::mutex> lock(G->tune_mu);
+      if (G->tuned_mid_cap >= 0) mid_cap = G->tuned_mid_cap;
+    }
     cfg = sampler_config(g, mdl);
     X.num_sms = cfg.num_sms;
     TRY(dev_alloc(&d_ctr, 1, X.st));
@@ -247,6 +260,13 @@ struct Sampler {
       CU(cudaMemsetAsync(slot_bitmap, 0, sizeof(uint32_t) * (size_t)words * (size_t)cfg.cta_blocks, X.st));
     }
     TRY(dev_alloc(&seed_bits, (size_t)words, X.st));
+    if (model == 0) {
+      const size_t warps = mid_tier_words(cfg);
+      TRY(dev_alloc(&mid_hash, warps * mid_hash_per_warp(), X.st));
+      CU(cudaMemsetAsync(mid_hash, 0, sizeof(uint32_t) * warps * mid_hash_per_warp(), X.st));
+      TRY(dev_alloc(&mid_queue, warps * mid_queue_per_warp(), X.st));
+      TRY(dev_alloc(&mid_slots, warps * mid_queue_per_warp(), X.st));
+    }
     if (benefit) {
       std::vector<uint64_t> pre((size_t)g.n + 1, 0);
       for (int64_t v = 0; v < g.n; ++v) pre[(size_t)v + 1] = pre[(size_t)v] + benefit[v];
@@ -263,6 +283,10 @@ struct Sampler {
     if (h_ctr) cudaFreeHost(h_ctr);
     h_ctr = nullptr;
     dev_free(big_list, st);
+    dev_free(mid_list, st);
+    dev_free(mid_hash, st);
+    dev_free(mid_queue, st);
+    dev_free(mid_slots, st);
     dev_free(fail_list, st);
     dev_free(redo_list, st);
     dev_free(slot_bitmap, st);
@@ -282,6 +306,11 @@ struct Sampler {
     J.count = count;
     J.bprefix = bprefix;
     J.big_list = big_list;
+    J.mid_cap = model == 0 ? mid_cap : 0;
+    J.mid_list = mid_list;
+    J.mid_hash = mid_hash;
+    J.mid_queue = mid_queue;
+    J.mid_slots = mid_slots;
     J.slot_bitmap = slot_bitmap;
     J.slot_queue = slot_queue;
     J.bitmap_words = (g.n + 31) / 32;
@@ -308,7 +337,7 @@ struct Sampler {
     h = X.begin(SSA_K_SAMPLE_CTA);
     CU(launch_sample_cta(J, cfg, X.st));
     X.end(h);
-    X.launches += 2;
+    X.launches += model == 0 ? 3 : 2;
     CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, X.st));
     CU(cudaStreamSynchronize(X.st));
     if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error");
@@ -330,6 +359,7 @@ struct Sampler {
     const int64_t j0 = P.count;
     if (j0 + count > (int64_t)0x7FFFFFFF) return fail(SSA_E_POOL_FULL, "more than 2^31 RR sets");
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&fail_list, &fail_cap, count, 0, X.st));
     TRY(dev_grow(&redo_list, &redo_cap, count, 0, X.st));
     if (j0 + count > P.cap_sets) {
@@ -412,6 +442,7 @@ struct Sampler {
   // Hit-test batch (Estimate-Inf): hit[i] = R_{j0+i} meets the seed bits.
   ssa_status hits(uint64_t seed, uint32_t stream, int64_t j0, int64_t count, Exec& X) {
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&hit, &hit_cap, count, 0, X.st));
     SampleJob J = job(seed, stream, j0, count);
     J.mode = MODE_HIT;
@@ -713,6 +744,56 @@ ssa_status estimate_inf_dev(Sampler& S, Cover& C, uint64_t seed, uint32_t stream
   return SSA_OK;
 }
 
+// IC sampler autotuner: time a pilot batch of RR sets under each candidate
+// hand-over size between the shared-memory warp tier, the global-memory warp
+// tier and the CTA tier, and keep the fastest for this graph.  The candidates
+// give identical sets (keyed randomness); only the time differs.
+ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, double* ms_out) {
+  const int cands[3] = {0, 2048, mid_tier_max_cap()};
+  double best_ms = 1e300;
+  int best = cands[2];
+  for (int c : cands) {
+    Sampler S;
+    DevPool P;
+    S.mid_cap = c;
+    ssa_status st = S.init(G, 0, nullptr, X);
+    S.mid_cap = c;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    if (st == SSA_OK) {
+      // one untimed pass sizes the pool, the second is timed
+      st = S.append(P, 0x5EEDull, 0, pilot, X);
+      if (st == SSA_OK) {
+        P.release(X.st);
+        P = DevPool();
+        cudaEventRecord(a, X.st);
+        st = S.append(P, 0x5EEDull, 0, pilot, X);
+        cudaEventRecord(b, X.st);
+      }
+    }
+    float ms = 0.f;
+    if (st == SSA_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    P.release(X.st);
+    S.release(X.st);
+    cudaStreamSynchronize(X.st);
+    if (st != SSA_OK) return st;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(G->tune_mu);
+    G->tuned_mid_cap = best;
+  }
+  if (chosen) *chosen = best;
+  if (ms_out) *ms_out = best_ms;
+  return SSA_OK;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 parameters (Table 1; Algorithm 1 lines 1-3; Algorithm 4 lines 1-3;
 // Eq. "set_ep").  Upsilon is taken from ln(1/delta) so that the tiny
@@ -790,6 +871,15 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
   const int k = p->k;
   const int64_t n = g->n;
   Params P = make_params(n, k, p->eps, p->delta, dssa);
+  if (p->model == SSA_IC) {
+    bool tuned;
+    {
+      std::lock_guard<std::mutex> lock(g->tune_mu);
+      tuned = g->tuned_mid_cap >= 0;
+    }
+    if (!tuned) TRY(autotune_ic(g, 8192, X, nullptr, nullptr));
+    X.launches = 0;
+  }
   Sampler S;
   DevPool pool;
   Cover C;
@@ -893,6 +983,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     out->cta_stored_entries = S.cta_store_nodes;
     out->cta_stored_sets = S.cta_store_sets;
     out->draws = S.draws;
+    out->mid_cap = p->model == SSA_IC ? S.mid_cap : 0;
     out->kernel_launches = X.launches;
     X.collect(out->kstats);
   } else {
@@ -1052,6 +1143,35 @@ ssa_solver* new_solver_keep_pool_memory() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   return new ssa_solver();
+}
+
+ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_samples, int32_t* mid_cap,
+                        double* pilot_ms) {
+  if (!g) return fail(SSA_E_ARG, "null graph");
+  if (model != SSA_IC) {
+    if (mid_cap) *mid_cap = 0;
+    return SSA_OK;  // the LT walk has one tier pair and nothing to tune
+  }
+  if (pilot_samples < 1) pilot_samples = 8192;
+  Exec X;
+  CU(cudaStreamCreateWithFlags(&X.st, cudaStreamNonBlocking));
+  int chosen = 0;
+  double ms = 0;
+  ssa_status st = autotune_ic(g, pilot_samples, X, &chosen, &ms);
+  cudaStreamSynchronize(X.st);
+  cudaStreamDestroy(X.st);
+  X.st = nullptr;
+  if (st != SSA_OK) return st;
+  if (mid_cap) *mid_cap = chosen;
+  if (pilot_ms) *pilot_ms = ms;
+  return SSA_OK;
+}
+
+ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap) {
+  if (!g || mid_cap < 0 || mid_cap > mid_tier_max_cap()) return fail(SSA_E_ARG, "mid_cap outside [0, 16384]");
+  std::lock_guard<std::mutex> lock(g->tune_mu);
+  g->tuned_mid_cap = mid_cap;
+  return SSA_OK;
 }
 
 ssa_status ssa_solver_create(const ssa_graph* g, void* stream, int64_t pool_bytes_cap, ssa_solver** out) {

@@ -21,6 +21,8 @@ struct GraphView {
 // Device counters of one sampling batch.
 struct Counters {
   unsigned long long work;         // warp tier: next sample index
+  unsigned long long mid_count;    // samples handed from the shared-memory warp tier to the global one
+  unsigned long long mid_work;     // global warp tier: next list index
   unsigned long long big_count;    // samples handed to the CTA tier
   unsigned long long big_work;     // CTA tier: next list index
   unsigned long long cursor;       // pool entries reserved (absolute)
@@ -57,6 +59,13 @@ struct SampleJob {
   // MODE_HIT: seed membership bits, per-sample flag (index j - j0)
   const uint32_t* seed_bits = nullptr;
   uint8_t* hit = nullptr;
+  // global-memory warp tier: hand-off list and per-warp hash / queue / slot scratch
+  int mid_cap = 0;               // sets above 512 nodes: 0 = straight to the CTA tier, else the
+                                 // global warp tier keeps sets up to mid_cap nodes (<= 16384)
+  int64_t* mid_list = nullptr;   // capacity `count`
+  uint32_t* mid_hash = nullptr;  // per warp: mid_hash_per_warp() words, zero between samples
+  int32_t* mid_queue = nullptr;  // per warp: mid_queue_per_warp()
+  uint32_t* mid_slots = nullptr; // per warp: mid_queue_per_warp()
   // CTA tier hand-off and scratch
   int64_t* big_list = nullptr;   // capacity `count`
   uint32_t* slot_bitmap = nullptr;  // per CTA slot: bitmap_words (unused when the bitmap is in smem)
@@ -69,6 +78,7 @@ struct LaunchCfg {
   int num_sms = 152;
   int warp_blocks = 0;   // grid of the warp tier
   int cta_blocks = 0;    // grid of the CTA tier (= number of scratch slots)
+  int mid_blocks = 0;    // grid of the global-memory warp tier
   int cta_threads = 1024;
   bool cta_smem_bitmap = false;
   int64_t smem_bitmap_bytes = 0;
@@ -85,6 +95,10 @@ cudaError_t build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_
 // ---- sampling -----------------------------------------------------------
 LaunchCfg sampler_config(const GraphView& g, int model);
 size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c);
+size_t mid_tier_words(const LaunchCfg& c);  // number of warps of the global-memory tier
+int mid_tier_max_cap();
+size_t mid_hash_per_warp();
+size_t mid_queue_per_warp();
 cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st);
 cudaError_t launch_sample_cta(const SampleJob& J, const LaunchCfg& c, cudaStream_t st);
 

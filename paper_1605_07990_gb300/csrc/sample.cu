@@ -76,19 +76,43 @@ __device__ __forceinline__ int32_t pick_root(const SampleJob& J, int64_t j) {
   return (int32_t)lo;
 }
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t u) { return (u * 0x9E3779B1u) >> 22; }  // 10 bits
+// Warp-per-sample tiers: 0 = hash and queue in shared memory (sets up to
+// 512 nodes), 1 = per-warp hash and queue in global memory (up to 16384
+// nodes).  Larger sets go on to the CTA tier.
+template <int TIER>
+struct Tier;
+template <>
+struct Tier<0> {
+  static constexpr int HBITS = 10, QCAP = WT_QCAP;
+};
+template <>
+struct Tier<1> {
+  static constexpr int HBITS = 15, QCAP = 16384;
+};
+constexpr int MID_HASH = 1 << Tier<1>::HBITS;
+constexpr int MID_QSLOTS = Tier<1>::QCAP + 32;  // queue/slot entries per warp (room for one round past the cap)
 
-// Insert u into the warp's hash set; true when u was not there.
-__device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u) {
+template <int HBITS>
+__device__ __forceinline__ uint32_t hash_slot(uint32_t u) {
+  return (u * 0x9E3779B1u) >> (32 - HBITS);
+}
+
+// Insert u into a warp's hash set of 2^HBITS slots; true when u was not
+// there, with its slot in *slot.
+template <int HBITS>
+__device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u, uint32_t* slot) {
   const uint32_t key = u + 1u;
-  uint32_t h = hash_slot(u);
-  for (int probe = 0; probe < WT_HASH; ++probe) {
+  uint32_t h = hash_slot<HBITS>(u);
+  for (int probe = 0; probe < (1 << HBITS); ++probe) {
     const uint32_t prev = atomicCAS(H + h, 0u, key);
-    if (prev == 0u) return true;
+    if (prev == 0u) {
+      *slot = h;
+      return true;
+    }
     if (prev == key) return false;
-    h = (h + 1u) & (WT_HASH - 1);
+    h = (h + 1u) & ((1u << HBITS) - 1u);
   }
-  return false;  // not reached: the table is never more than 5/8 full
+  return false;  // not reached: the table is never more than half full
 }
 
 // Edge-balanced expansion of up to 32 frontier nodes (lane i holds node v or
@@ -222,47 +246,66 @@ __device__ __forceinline__ void warp_store_set(const SampleJob& J, int64_t j, co
   }
 }
 
-template <int MODE>
+template <int MODE, int TIER>
 __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
-  __shared__ __align__(16) uint32_t s_hash[WT_WARPS][WT_HASH];
-  __shared__ int32_t s_q[WT_WARPS][WT_QCAP];
+  constexpr int HBITS = Tier<TIER>::HBITS, QCAP = Tier<TIER>::QCAP;
+  __shared__ __align__(16) uint32_t s_hash[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_HASH : 4];
+  __shared__ int32_t s_q[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_QCAP : 4];
   __shared__ uint32_t s_stage[WT_WARPS][STAGE];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* H = s_hash[wid];
-  int32_t* Q = s_q[wid];
-  uint4* H4 = reinterpret_cast<uint4*>(H);
-  for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
+  const size_t gwarp = (size_t)blockIdx.x * WT_WARPS + wid;
+  uint32_t* H = TIER == 0 ? s_hash[wid] : J.mid_hash + gwarp * MID_HASH;
+  int32_t* Q = TIER == 0 ? s_q[wid] : J.mid_queue + gwarp * MID_QSLOTS;
+  uint32_t* slots = TIER == 0 ? nullptr : J.mid_slots + gwarp * MID_QSLOTS;
+  if (TIER == 0) {
+    uint4* H4 = reinterpret_cast<uint4*>(H);
+    for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
+  }
   __syncwarp();
+  // tier 0 takes the batch's samples, tier 1 the ones tier 0 handed over
+  const unsigned long long count =
+      TIER == 0 ? (unsigned long long)J.count : *((volatile unsigned long long*)&J.ctr->mid_count);
+  unsigned long long* work = TIER == 0 ? &J.ctr->work : &J.ctr->mid_work;
   unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
     unsigned long long idx = 0;
-    if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
+    if (lane == 0) idx = atomicAdd(work, 1ull);
     idx = __shfl_sync(FULL_MASK, idx, 0);
-    if (idx >= (unsigned long long)J.count) break;
-    const int64_t j = sample_at(J, idx);
+    if (idx >= count) break;
+    const int64_t j = TIER == 0 ? sample_at(J, idx) : J.mid_list[idx];
     const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) {
-      H[hash_slot((uint32_t)root)] = (uint32_t)root + 1u;
+      const uint32_t h0 = hash_slot<HBITS>((uint32_t)root);
+      H[h0] = (uint32_t)root + 1u;
       Q[0] = root;
+      if (TIER == 1) slots[0] = h0;
     }
     int tail = 1, head = 0;
     bool overflow = false;
     bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
+    // tier 1's hand-over size is tuned at run time (at most its queue capacity)
+    const int cap = TIER == 0 ? QCAP : min(QCAP, J.mid_cap);
     __syncwarp();
     auto known = [](uint32_t) { return false; };
     auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
-      const bool is_new = (u != NO_NODE) && hash_insert(H, u);
+      uint32_t slot = 0;
+      const bool is_new = (u != NO_NODE) && hash_insert<HBITS>(H, u, &slot);
       const unsigned m = __ballot_sync(FULL_MASK, is_new);
       bool h = false;
       if (is_new) {
         const int pos = tail + __popc(m & lt_mask);
-        if (pos < WT_QCAP) Q[pos] = (int32_t)u;
+        if (TIER == 0) {
+          if (pos < QCAP) Q[pos] = (int32_t)u;
+        } else {
+          Q[pos] = (int32_t)u;  // pos <= cap + 31 < QCAP + 32: room for one round past the cap
+          slots[pos] = slot;
+        }
         if (MODE == MODE_HIT) h = test_bit(J.seed_bits, u);
       }
       tail += __popc(m);
       if (MODE == MODE_HIT) hit = __any_sync(FULL_MASK, h) || hit;
-      if (tail > WT_QCAP) overflow = true;
+      if (tail > cap) overflow = true;
       return overflow || hit;
     };
     while (head < tail && !overflow && !hit) {
@@ -276,8 +319,13 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
     __syncwarp();
     if (overflow) {
       if (lane == 0) {
-        const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
-        J.big_list[b] = j;
+        if (TIER == 0 && J.mid_cap > 0) {
+          const unsigned long long b = atomicAdd(&J.ctr->mid_count, 1ull);
+          J.mid_list[b] = j;
+        } else {
+          const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
+          J.big_list[b] = j;
+        }
       }
     } else {
       if (MODE == MODE_STORE) warp_store_set(J, j, Q, tail, lane);
@@ -285,7 +333,13 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       if (lane == 0) nv += (unsigned long long)tail;
     }
     __syncwarp();
-    for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
+    if (TIER == 0) {
+      uint4* H4 = reinterpret_cast<uint4*>(H);
+      for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
+    } else {
+      // clear only the slots this sample used (tail <= QCAP + 32 entries recorded)
+      for (int i = lane; i < tail; i += 32) H[slots[i]] = 0u;
+    }
     __syncwarp();
   }
   flush_stats(J.ctr, ev, nv, dr, lane, false);
@@ -387,7 +441,11 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
     __syncthreads();
     if (J.model == 0) {
       const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
-      auto known = [&](uint32_t u) { return ((*(volatile uint32_t*)(bits + (u >> 5))) >> (u & 31)) & 1u; };
+      // a stale 0 only costs a draw; bits are never cleared during a sample
+      auto known = [&](uint32_t u) {
+        const uint32_t w = SMEM_BITMAP ? bits[u >> 5] : __ldcg(bits + (u >> 5));
+        return (w >> (u & 31)) & 1u;
+      };
       auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
         bool is_new = false;
         if (u != NO_NODE) {
@@ -496,7 +554,7 @@ LaunchCfg sampler_config(const GraphView& g, int model) {
   cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
   if (model == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE>, WT_WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE, 0>, WT_WARPS * 32, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_lt<MODE_STORE>, WT_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
@@ -506,8 +564,14 @@ LaunchCfg sampler_config(const GraphView& g, int model) {
   c.cta_smem_bitmap = c.smem_bitmap_bytes <= SMEM_BITMAP_MAX_BYTES;
   c.cta_threads = 1024;
   c.cta_blocks = c.num_sms;
+  c.mid_blocks = c.num_sms * 2;  // 16 warps per SM, each with its own global hash and queue
   return c;
 }
+
+size_t mid_tier_words(const LaunchCfg& c) { return (size_t)c.mid_blocks * WT_WARPS; }
+int mid_tier_max_cap() { return Tier<1>::QCAP; }
+size_t mid_hash_per_warp() { return MID_HASH; }
+size_t mid_queue_per_warp() { return MID_QSLOTS; }
 
 size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c) {
   const size_t words = (size_t)((g.n + 31) / 32);
@@ -518,8 +582,13 @@ size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c) {
 cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
   const dim3 grid(c.warp_blocks), block(WT_WARPS * 32);
   if (J.model == 0) {
-    if (J.mode == MODE_STORE) k_sample_warp_ic<MODE_STORE><<<grid, block, 0, st>>>(J);
-    else k_sample_warp_ic<MODE_HIT><<<grid, block, 0, st>>>(J);
+    if (J.mode == MODE_STORE) {
+      k_sample_warp_ic<MODE_STORE, 0><<<grid, block, 0, st>>>(J);
+      if (J.mid_cap > 0) k_sample_warp_ic<MODE_STORE, 1><<<c.mid_blocks, block, 0, st>>>(J);
+    } else {
+      k_sample_warp_ic<MODE_HIT, 0><<<grid, block, 0, st>>>(J);
+      if (J.mid_cap > 0) k_sample_warp_ic<MODE_HIT, 1><<<c.mid_blocks, block, 0, st>>>(J);
+    }
   } else {
     if (J.mode == MODE_STORE) k_sample_warp_lt<MODE_STORE><<<grid, block, 0, st>>>(J);
     else k_sample_warp_lt<MODE_HIT><<<grid, block, 0, st>>>(J);
