@@ -26,6 +26,9 @@ constexpr int WT_HASH = 1024;    // hash slots per warp (power of two)
 constexpr int WT_QCAP = 512;     // largest IC set kept in the warp tier
 constexpr int LT_QCAP = 1024;    // largest LT walk kept in the warp tier
 constexpr int STAGE = 128;       // live candidates of one slab (32 lanes x 4 edges)
+constexpr int WARP_HEAVY_GROUPS = 4096;  // warp tiers hand samples meeting longer in-lists to the CTA tier
+constexpr int CTA_HEAVY_GROUPS = 512;    // the CTA tier splits longer in-lists over all its warps
+constexpr int CTA_HEAVY_CAP = 256;       // heavy in-lists per level shared this way
 
 constexpr uint32_t PHILOX_M0 = 0xD2511F53u, PHILOX_M1 = 0xCD9E8D57u;
 
@@ -115,26 +118,91 @@ __device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u, uint32_t* s
   return false;  // not reached: the table is never more than half full
 }
 
-// Edge-balanced expansion of up to 32 frontier nodes (lane i holds node v or
-// -1).  Live in-edges whose tail may be new are compacted through `stage`
-// (STAGE entries, private to the warp) and handed to visit(u) in rounds of 32
-// (NO_NODE for idle lanes); visit returns a warp-uniform "stop".  known(u)
-// may report nodes already in the set so their edges need no draw.
+// One slab: each lane holds one 4-edge group `grp` of an in-list [olo, ohi)
+// (when `valid`).  Edges whose tail may be new draw their coins; the live
+// ones are compacted through `stage` (STAGE entries, private to the warp) and
+// handed to visit(u) in rounds of 32 (NO_NODE for idle lanes).  known(u) may
+// report tails already in the set so their edges need no draw.  Returns the
+// warp-uniform "stop" of visit.
 template <class Known, class Visit>
-__device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
-                                          int lane, uint32_t* stage, unsigned long long& ev,
-                                          unsigned long long& draws, Known&& known, Visit&& visit) {
+__device__ __forceinline__ bool process_slab(const GraphView& g, bool valid, uint32_t grp, uint32_t olo, uint32_t ohi,
+                                             const uint32_t* rk, const SampleConst& sc, int lane, uint32_t* stage,
+                                             unsigned long long& draws, Known&& known, Visit&& visit) {
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint32_t cand = 0, u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+  if (valid) {
+    const uint32_t e = grp * 4u;
+    // edges e..e+3 that belong to the in-list
+    const uint32_t a = olo > e ? olo - e : 0u;
+    const uint32_t b = ohi - e;
+    uint32_t need = (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
+    const uint4* p = reinterpret_cast<const uint4*>(g.edge) + (size_t)grp * 2;
+    const uint4 A = __ldg(p), B = __ldg(p + 1);
+    u0 = A.x; u1 = A.z; u2 = B.x; u3 = B.z;
+    if ((need & 1u) && known(u0)) need &= ~1u;
+    if ((need & 2u) && known(u1)) need &= ~2u;
+    if ((need & 4u) && known(u2)) need &= ~4u;
+    if ((need & 8u) && known(u3)) need &= ~8u;
+    if (need) {
+      ++draws;
+      const uint4 r = philox_x(grp, sc, rk);
+      if ((need & 1u) && edge_live(r.x, A.y)) cand |= 1u;
+      if ((need & 2u) && edge_live(r.y, A.w)) cand |= 2u;
+      if ((need & 4u) && edge_live(r.z, B.y)) cand |= 4u;
+      if ((need & 8u) && edge_live(r.w, B.w)) cand |= 8u;
+    }
+  }
+  const unsigned any = __ballot_sync(FULL_MASK, cand != 0u);
+  if (!any) return false;
+  if (!__any_sync(FULL_MASK, (cand & (cand - 1u)) != 0u)) {
+    // at most one candidate per lane (the common case): no staging
+    const uint32_t u = !cand ? NO_NODE : (cand & 1u) ? u0 : (cand & 2u) ? u1 : (cand & 4u) ? u2 : u3;
+    return visit(u, lt_mask);
+  }
+  const int c = __popc(cand);
+  const int cin = warp_inclusive_scan(c, lane);
+  const int ctot = __shfl_sync(FULL_MASK, cin, 31);
+  int pos = cin - c;
+  if (cand & 1u) stage[pos++] = u0;
+  if (cand & 2u) stage[pos++] = u1;
+  if (cand & 4u) stage[pos++] = u2;
+  if (cand & 8u) stage[pos++] = u3;
+  __syncwarp();
+  bool stop = false;
+  for (int s0 = 0; s0 < ctot && !stop; s0 += 32) {
+    const uint32_t u = (s0 + lane < ctot) ? stage[s0 + lane] : NO_NODE;
+    stop = visit(u, lt_mask);
+  }
+  __syncwarp();
+  return stop;
+}
+
+// Edge-balanced expansion of up to 32 frontier nodes (lane i holds node v or
+// -1): their in-edge ranges are cut into 4-edge groups dealt to lanes by a
+// warp prefix sum.  A node with more than heavy_groups groups is first offered
+// to take_heavy(v, lo, hi, ng) (per lane); when it takes the node, the node is
+// skipped here.  Returns 0, 1 when visit asked to stop, or 2 when
+// take_heavy(...) == HEAVY_ABORT for some lane (the caller hands the sample on).
+constexpr int HEAVY_SKIP = 1, HEAVY_ABORT = 2;
+
+template <class Known, class Visit, class Heavy>
+__device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
+                                         int lane, uint32_t* stage, unsigned long long& ev, unsigned long long& draws,
+                                         int heavy_groups, Known&& known, Visit&& visit, Heavy&& take_heavy) {
   uint32_t lo = 0, hi = 0;  // edge positions fit 32 bits (m < 2^31)
   if (v >= 0) {
     lo = (uint32_t)__ldg(g.off + v);
     hi = (uint32_t)__ldg(g.off + v + 1);
   }
-  ev += hi - lo;
-  const int ng = (hi > lo) ? (int)(((hi + 3) >> 2) - (lo >> 2)) : 0;
+  int ng = (hi > lo) ? (int)(((hi + 3) >> 2) - (lo >> 2)) : 0;
+  int heavy = 0;
+  if (ng > heavy_groups) heavy = take_heavy(v, lo, hi, ng);
+  if (__any_sync(FULL_MASK, heavy == HEAVY_ABORT)) return 2;
+  if (heavy == HEAVY_SKIP) ng = 0;  // counted and expanded by the taker
+  else ev += hi - lo;
   const int incl = warp_inclusive_scan(ng, lane);
   const int excl = incl - ng;
   const int total = __shfl_sync(FULL_MASK, incl, 31);
-  const unsigned lt_mask = (1u << lane) - 1u;
   for (int base = 0; base < total; base += 32) {
     const int q = base + lane;
     int owner = 0;
@@ -147,56 +215,10 @@ __device__ __forceinline__ bool expand_ic(const GraphView& g, int32_t v, const u
     const uint32_t olo = __shfl_sync(FULL_MASK, lo, owner);
     const uint32_t ohi = __shfl_sync(FULL_MASK, hi, owner);
     const int oex = __shfl_sync(FULL_MASK, excl, owner);
-    uint32_t cand = 0, u0 = 0, u1 = 0, u2 = 0, u3 = 0;
-    if (q < total) {
-      const uint32_t grp = (olo >> 2) + (uint32_t)(q - oex);
-      const uint32_t e = grp * 4u;
-      // edges e..e+3 that belong to the owner's in-list
-      const uint32_t a = olo > e ? olo - e : 0u;
-      const uint32_t b = ohi - e;
-      uint32_t need = (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
-      const uint4* p = reinterpret_cast<const uint4*>(g.edge) + (size_t)grp * 2;
-      const uint4 A = __ldg(p), B = __ldg(p + 1);
-      u0 = A.x; u1 = A.z; u2 = B.x; u3 = B.z;
-      if ((need & 1u) && known(u0)) need &= ~1u;
-      if ((need & 2u) && known(u1)) need &= ~2u;
-      if ((need & 4u) && known(u2)) need &= ~4u;
-      if ((need & 8u) && known(u3)) need &= ~8u;
-      if (need) {
-        ++draws;
-        const uint4 r = philox_x(grp, sc, rk);
-        if ((need & 1u) && edge_live(r.x, A.y)) cand |= 1u;
-        if ((need & 2u) && edge_live(r.y, A.w)) cand |= 2u;
-        if ((need & 4u) && edge_live(r.z, B.y)) cand |= 4u;
-        if ((need & 8u) && edge_live(r.w, B.w)) cand |= 8u;
-      }
-    }
-    const unsigned any = __ballot_sync(FULL_MASK, cand != 0u);
-    if (!any) continue;
-    if (!__any_sync(FULL_MASK, (cand & (cand - 1u)) != 0u)) {
-      // at most one candidate per lane (the common case): no staging
-      const uint32_t u = !cand ? NO_NODE : (cand & 1u) ? u0 : (cand & 2u) ? u1 : (cand & 4u) ? u2 : u3;
-      if (visit(u, lt_mask)) return true;
-      continue;
-    }
-    const int c = __popc(cand);
-    const int cin = warp_inclusive_scan(c, lane);
-    const int ctot = __shfl_sync(FULL_MASK, cin, 31);
-    int pos = cin - c;
-    if (cand & 1u) stage[pos++] = u0;
-    if (cand & 2u) stage[pos++] = u1;
-    if (cand & 4u) stage[pos++] = u2;
-    if (cand & 8u) stage[pos++] = u3;
-    __syncwarp();
-    bool stop = false;
-    for (int s0 = 0; s0 < ctot && !stop; s0 += 32) {
-      const uint32_t u = (s0 + lane < ctot) ? stage[s0 + lane] : NO_NODE;
-      stop = visit(u, lt_mask);
-    }
-    __syncwarp();
-    if (stop) return true;
+    const uint32_t grp = (olo >> 2) + (uint32_t)(q - oex);
+    if (process_slab(g, q < total, grp, olo, ohi, rk, sc, lane, stage, draws, known, visit)) return 1;
   }
-  return false;
+  return 0;
 }
 
 __device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev, unsigned long long nv,
@@ -308,16 +330,27 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       if (tail > cap) overflow = true;
       return overflow || hit;
     };
+    // a node with a very long in-list needs many warps: hand the sample to the CTA tier
+    auto to_cta = [](int32_t, uint32_t, uint32_t, int) { return HEAVY_ABORT; };
+    bool handoff = false;
     while (head < tail && !overflow && !hit) {
       const int cnt = min(32, tail - head);
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, known, visit);
+      if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, WARP_HEAVY_GROUPS, known, visit, to_cta) == 2) {
+        handoff = true;
+        break;
+      }
       head += cnt;
     }
     __syncwarp();
-    if (overflow) {
+    if (handoff) {
+      if (lane == 0) {
+        const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
+        J.big_list[b] = j;
+      }
+    } else if (overflow) {
       if (lane == 0) {
         if (TIER == 0 && J.mid_cap > 0) {
           const unsigned long long b = atomicAdd(&J.ctr->mid_count, 1ull);
@@ -415,6 +448,10 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
   __shared__ int s_tail, s_next, s_hit, s_ok;
   __shared__ unsigned long long s_pos;
   __shared__ uint32_t s_stage[32][STAGE];
+  // heavy in-lists of the current level, expanded by all warps together
+  __shared__ uint32_t s_hlo[CTA_HEAVY_CAP], s_hhi[CTA_HEAVY_CAP];
+  __shared__ int s_hpref[CTA_HEAVY_CAP];
+  __shared__ int s_nheavy, s_htotal, s_hnext;
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
   const int64_t n = J.g.n;
   uint32_t* bits = SMEM_BITMAP ? s_bits : J.slot_bitmap + (size_t)blockIdx.x * (size_t)J.bitmap_words;
@@ -465,6 +502,16 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
         if (MODE == MODE_HIT) return __any_sync(FULL_MASK, *(volatile int*)&s_hit != 0);
         return false;
       };
+      auto take_heavy = [&](int32_t, uint32_t lo, uint32_t hi, int) -> int {
+        const int slot = atomicAdd(&s_nheavy, 1);
+        if (slot >= CTA_HEAVY_CAP) return 0;  // list full: this warp expands it itself
+        s_hlo[slot] = lo;
+        s_hhi[slot] = hi;
+        ev += hi - lo;
+        return HEAVY_SKIP;
+      };
+      const int wid = tid >> 5, nwarp = nthr >> 5;
+      if (tid == 0) s_nheavy = 0;
       int lvl_begin = 0, lvl_end = 1;
       for (;;) {
         // every thread is past the previous barrier and nobody writes s_hit
@@ -479,13 +526,50 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
           if (b >= lvl_end) break;
           const int cnt = min(32, lvl_end - b);
           const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
-          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, dr, known, visit)) break;
+          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy)) break;
         }
         __syncthreads();
+        const int nh = min(s_nheavy, CTA_HEAVY_CAP);
+        if (nh > 0 && !s_hit) {
+          // groups of the heavy in-lists, dealt to all warps 32 at a time
+          if (wid == 0) {
+            int carry = 0;
+            for (int base = 0; base < nh; base += 32) {
+              const int i = base + lane;
+              const int ng = i < nh ? (int)(((s_hhi[i] + 3) >> 2) - (s_hlo[i] >> 2)) : 0;
+              const int incl = warp_inclusive_scan(ng, lane);
+              if (i < nh) s_hpref[i] = carry + incl - ng;
+              carry += __shfl_sync(FULL_MASK, incl, 31);
+            }
+            if (lane == 0) {
+              s_htotal = carry;
+              s_hnext = 0;
+            }
+          }
+          __syncthreads();
+          const int htotal = s_htotal;
+          for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&s_hnext, 32);
+            c = __shfl_sync(FULL_MASK, c, 0);
+            if (c >= htotal) break;
+            const int q = c + lane;
+            int it = 0;  // last heavy list whose first group is <= q
+            for (int step = CTA_HEAVY_CAP / 2; step; step >>= 1)
+              if (it + step < nh && s_hpref[it + step] <= q) it += step;
+            const uint32_t olo = s_hlo[it], ohi = s_hhi[it];
+            const uint32_t grp = (olo >> 2) + (uint32_t)(q - s_hpref[it]);
+            if (process_slab(J.g, q < htotal, grp, olo, ohi, J.rk, sc, lane, stage, dr, known, visit)) break;
+          }
+        }
+        __syncthreads();
+        if (tid == 0) s_nheavy = 0;
         lvl_begin = lvl_end;
         lvl_end = s_tail;
         __syncthreads();
       }
+      (void)wid;
+      (void)nwarp;
     } else if (tid == 0) {
       const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_LT, J.stream, j));
       int32_t cur = root;
