@@ -34,6 +34,7 @@ WORKLOADS = {
     "dssa_ic_trivalency_rmat20_m16M_k100": (20, 1 << 24, 1, 1, 0, 100, 0.1),
     "ssa_ic_wc_rmat14_m128K_k50": (14, 1 << 17, 0, 0, 0, 50, 0.1),
     "dssa_lt_wc_rmat23_m128M_k500": (23, 1 << 27, 0, 1, 1, 500, 0.05),
+    "ssa_ic_wc_rmat25_m1.3G_k100": (25, 1_300_000_000, 0, 0, 0, 100, 0.1),
 }
 DEFAULT = "dssa_ic_trivalency_rmat20_m16M_k100"
 METRIC, UNIT = "RR sets/s", "RR sets/s"
@@ -360,8 +361,11 @@ def main():
     roof = None
     if abytes is not None and ks[dom]["ms"] > 0:
         ach = abytes / (ks[dom]["ms"] / 1000.0) / 1e9
+        # DRAM bytes per CTA-tier launch of one solve, from the ncu capture summarised in
+        # profiles/sample_cta_dssa_ic_trivalency_rmat20.md (valid for this kernel build and workload)
+        traffic = 2.32e10 if (dom == "sample_cta" and name == DEFAULT) else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_source": peak_kind, "traffic": None,
+                "peak_source": peak_kind, "traffic": traffic,
                 "bytes_per_launch": abytes / max(1, ks[dom]["launches"]),
                 "avg_launch_ms": ks[dom]["ms"] / max(1, ks[dom]["launches"])}
 

@@ -99,3 +99,34 @@ def test_c2_estimate_inf_full_size(c2):
     gT, gh = P.ssa_estimate_inf(gg, P.SSA_IC, 1, 3, S, 150.5, 4000)
     oT, oh, _ = oracle.estimate_inf(og, oracle.IC, 1, 3, S, 150.5, 4000)
     assert (gT, gh) == (oT, oh)
+
+
+def test_c4_billion_edges_sampled():
+    """SSA, WC-IC, R-MAT 2^25 nodes / 1.3e9 draws (1,263,509,823 edges): sampled RR sets and an
+    Estimate-Inf run against the oracle (built on the host from the same edge list), and the SSA
+    solve's final greedy against ssa_max_coverage on the same sets."""
+    el = inputs.rmat(25, 1_300_000_000, seed=1)
+    assert el.m > 1_200_000_000
+    gg = P.ssa_load_graph(el.n, el.src, el.dst, None, P.SSA_W_WC)
+    og = oracle.Graph(el.n, el.src, el.dst, oracle.W_WC)
+    del el
+    n = 1 << 25
+    s = P.Solver(gg)
+    r = s.solve(P.SSA_ALGO_SSA, P.SSA_IC, 100, 0.1, 1.0 / n, 1)
+    N = r.trace[-1]["n_sets"]
+    pool = P.Pool(gg, P.SSA_IC, seed=1).grow(N)
+    seeds, gains, cov = pool.max_coverage(N, 100)
+    assert np.array_equal(seeds, r.seeds) and cov == r.trace[-1]["cov"]
+    rng = np.random.default_rng(11)
+    sizes = pool.set_sizes(0, N)
+    big = np.argsort(sizes)[-6:]
+    for j in np.concatenate([rng.choice(N, 30, replace=False), big]):
+        oset = oracle.rr_set(og, oracle.IC, 1, 0, int(j))
+        gset = np.sort(pool.sets(int(j), 1)[0])
+        assert np.array_equal(oset, gset), j
+    S = r.seeds[:20]
+    assert P.ssa_estimate_inf(gg, P.SSA_IC, 1, 4, S, 60.5, 3000) == \
+        oracle.estimate_inf(og, oracle.IC, 1, 4, S, 60.5, 3000)[:2]
+    pool.free()
+    s.free()
+    gg.free()
