@@ -102,16 +102,20 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
 
 /* IC sampler tuning.  An RR set is built by one warp while it stays within
  * 512 nodes (shared-memory hash), then -- up to mid_cap nodes -- by one warp
- * with a global-memory hash, then by a whole CTA with an n-bit bitmap.  The
- * best mid_cap depends on the graph's set-size mix (wide, bimodal sets favour
- * 0; deep chains favour 16384).  ssa_autotune times a pilot batch of
- * pilot_samples sets (0 = 8192) under the candidates {0, 2048, 16384} and
- * keeps the fastest in the graph handle; a solve on an untuned graph tunes it
- * first.  ssa_set_tuning fixes mid_cap (0..16384) by hand.  Results never
- * depend on the tuning.  For SSA_LT ssa_autotune has nothing to tune. */
+ * with a global-memory hash, then by a whole CTA with an n-bit bitmap that
+ * splits long in-lists over all its warps.  A warp that meets an in-list of
+ * more than heavy_groups 4-edge groups hands its sample to the CTA tier.  The
+ * best values depend on the graph (wide bimodal sets favour mid_cap 0; deep
+ * chains favour 16384; hubs of millions of in-edges favour an early hand-over).
+ * ssa_autotune times a pilot batch of pilot_samples sets (0 = 8192) under the
+ * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never} and keeps
+ * the fastest in the graph handle; a solve on an untuned graph tunes it first.
+ * ssa_set_tuning fixes both by hand (0 <= mid_cap <= 16384, heavy_groups >= 1;
+ * 0x7FFFFFFF = never hand over).  Results never depend on the tuning.  For
+ * SSA_LT ssa_autotune has nothing to tune. */
 ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_samples, int32_t* mid_cap,
                         double* pilot_ms);
-ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap);
+ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap, int32_t heavy_groups);
 
 /* ------------------------------------------------------------------------ */
 /* Solve (Definition 1: IM; Algorithm 1 SSA; Algorithm 4 D-SSA).            */
@@ -174,6 +178,7 @@ typedef struct {
   int64_t cta_stored_sets;   /* sets that tier wrote to the pool */
   int64_t draws;             /* Philox draws: IC 4-edge groups that needed coins, LT picks */
   int32_t mid_cap;           /* IC sampler hand-over size used (see ssa_autotune) */
+  int32_t heavy_groups;      /* IC: in-list length (4-edge groups) above which warp tiers hand over */
   int64_t kernel_launches;   /* CUDA kernels this library launched for the solve */
   double seconds;            /* host wall time of the call */
   int32_t want_kstats;       /* in: 1 to time kernel classes with CUDA events */

@@ -50,7 +50,7 @@ class ssa_result(C.Structure):
                 ("pool_entries", C.c_int64), ("edge_visits", C.c_int64), ("node_visits", C.c_int64),
                 ("cta_sets", C.c_int64), ("cta_edge_visits", C.c_int64), ("cta_node_visits", C.c_int64),
                 ("cta_stored_entries", C.c_int64), ("cta_stored_sets", C.c_int64), ("draws", C.c_int64),
-                ("mid_cap", C.c_int32),
+                ("mid_cap", C.c_int32), ("heavy_groups", C.c_int32),
                 ("kernel_launches", C.c_int64), ("seconds", C.c_double), ("want_kstats", C.c_int32),
                 ("kstats", ssa_kstat * 5)]
 
@@ -71,7 +71,7 @@ EXPORTS = {
     "ssa_graph_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssa_graph_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssa_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
-    "ssa_set_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ssa_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "ssa_solver_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
@@ -190,8 +190,8 @@ def ssa_autotune(g: Graph, model=SSA_IC, pilot_samples=0):
     return cap.value, ms.value
 
 
-def ssa_set_tuning(g: Graph, mid_cap):
-    _check(lib().ssa_set_tuning(g.h, int(mid_cap)))
+def ssa_set_tuning(g: Graph, mid_cap, heavy_groups=0x7FFFFFFF):
+    _check(lib().ssa_set_tuning(g.h, int(mid_cap), int(heavy_groups)))
 
 
 # ---- solve ----
@@ -213,6 +213,7 @@ class Result:
     cta_stored_sets: int = 0
     draws: int = 0
     mid_cap: int = 0
+    heavy_groups: int = 0
     trace: list = field(default_factory=list)
     kstats: dict = field(default_factory=dict)
 
@@ -242,7 +243,8 @@ def _unpack(r, seeds, tr):
     ks = {KERNEL_CLASSES[i]: {"launches": r.kstats[i].launches, "ms": r.kstats[i].ms} for i in range(5)}
     return Result(seeds.copy(), r.influence, r.rounds, r.n_rr, r.pool_entries, r.edge_visits, r.node_visits,
                   r.kernel_launches, r.seconds, r.cta_sets, r.cta_edge_visits, r.cta_node_visits,
-                  r.cta_stored_entries, r.cta_stored_sets, r.draws, r.mid_cap, trace, ks)
+                  r.cta_stored_entries, r.cta_stored_sets, r.draws, r.mid_cap, r.heavy_groups,
+                  trace, ks)
 
 
 def ssa_solve(g: Graph, algo, model, k, eps, delta, seed, benefit=None, pool_bytes_cap=0, want_kstats=False,

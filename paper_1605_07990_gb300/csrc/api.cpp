@@ -96,9 +96,10 @@ struct ssa_graph {
   int64_t* off = nullptr;
   uint2* edge = nullptr;
   int64_t bytes = 0;
-  // IC sampler hand-over size chosen by the autotuner (-1: not tuned yet)
+  // IC sampler hand-over sizes chosen by the autotuner (-1: not tuned yet)
   mutable std::mutex tune_mu;
   mutable int tuned_mid_cap = -1;
+  mutable int tuned_heavy = 0x7FFFFFFF;
   GraphView view() const {
     GraphView v;
     v.n = n;
@@ -227,6 +228,7 @@ struct Sampler {
   uint64_t* bprefix = nullptr;
   uint64_t wsum = 0;
   int mid_cap = 16384;  // IC: largest set the global warp tier keeps (0 = none)
+  int heavy_groups = 0x7FFFFFFF;  // IC: warp tiers hand samples with longer in-lists to the CTA tier
   int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
   int64_t cta_edge_visits = 0, cta_node_visits = 0, cta_samples = 0;
   int64_t cta_store_nodes = 0, cta_store_sets = 0;  // the CTA tier's sets written to the pool
@@ -247,7 +249,10 @@ struct Sampler {
     model = mdl;
     {
       std::lock_guard<std::mutex> lock(G->tune_mu);
-      if (G->tuned_mid_cap >= 0) mid_cap = G->tuned_mid_cap;
+      if (G->tuned_mid_cap >= 0) {
+        mid_cap = G->tuned_mid_cap;
+        heavy_groups = G->tuned_heavy;
+      }
     }
     cfg = sampler_config(g, mdl);
     X.num_sms = cfg.num_sms;
@@ -307,6 +312,7 @@ struct Sampler {
     J.bprefix = bprefix;
     J.big_list = big_list;
     J.mid_cap = model == 0 ? mid_cap : 0;
+    J.warp_heavy_groups = heavy_groups;
     J.mid_list = mid_list;
     J.mid_hash = mid_hash;
     J.mid_queue = mid_queue;
@@ -749,15 +755,17 @@ ssa_status estimate_inf_dev(Sampler& S, Cover& C, uint64_t seed, uint32_t stream
 // tier and the CTA tier, and keep the fastest for this graph.  The candidates
 // give identical sets (keyed randomness); only the time differs.
 ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, double* ms_out) {
-  const int cands[3] = {0, 2048, mid_tier_max_cap()};
+  // (mid_cap, heavy in-list hand-over in 4-edge groups; 0x7FFFFFFF = never)
+  const int cands[4][2] = {{0, 0x7FFFFFFF}, {mid_tier_max_cap(), 0x7FFFFFFF}, {0, 4096}, {mid_tier_max_cap(), 4096}};
   double best_ms = 1e300;
-  int best = cands[2];
-  for (int c : cands) {
+  int best = cands[1][0], best_heavy = cands[1][1];
+  for (const auto& cand : cands) {
+    const int c = cand[0];
     Sampler S;
     DevPool P;
-    S.mid_cap = c;
     ssa_status st = S.init(G, 0, nullptr, X);
     S.mid_cap = c;
+    S.heavy_groups = cand[1];
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -783,11 +791,13 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
     if (ms < best_ms) {
       best_ms = ms;
       best = c;
+      best_heavy = cand[1];
     }
   }
   {
     std::lock_guard<std::mutex> lock(G->tune_mu);
     G->tuned_mid_cap = best;
+    G->tuned_heavy = best_heavy;
   }
   if (chosen) *chosen = best;
   if (ms_out) *ms_out = best_ms;
@@ -984,6 +994,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     out->cta_stored_sets = S.cta_store_sets;
     out->draws = S.draws;
     out->mid_cap = p->model == SSA_IC ? S.mid_cap : 0;
+    out->heavy_groups = p->model == SSA_IC ? S.heavy_groups : 0;
     out->kernel_launches = X.launches;
     X.collect(out->kstats);
   } else {
@@ -1167,10 +1178,12 @@ ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_sampl
   return SSA_OK;
 }
 
-ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap) {
+ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap, int32_t heavy_groups) {
   if (!g || mid_cap < 0 || mid_cap > mid_tier_max_cap()) return fail(SSA_E_ARG, "mid_cap outside [0, 16384]");
+  if (heavy_groups < 1) return fail(SSA_E_ARG, "heavy_groups must be >= 1");
   std::lock_guard<std::mutex> lock(g->tune_mu);
   g->tuned_mid_cap = mid_cap;
+  g->tuned_heavy = heavy_groups;
   return SSA_OK;
 }
 

@@ -60,6 +60,8 @@ struct SampleJob {
   const uint32_t* seed_bits = nullptr;
   uint8_t* hit = nullptr;
   // global-memory warp tier: hand-off list and per-warp hash / queue / slot scratch
+  int warp_heavy_groups = 0x7FFFFFFF;  // warp tiers hand samples meeting an in-list of more 4-edge
+                                       // groups than this to the CTA tier (tuned)
   int mid_cap = 0;               // sets above 512 nodes: 0 = straight to the CTA tier, else the
                                  // global warp tier keeps sets up to mid_cap nodes (<= 16384)
   int64_t* mid_list = nullptr;   // capacity `count`

@@ -26,7 +26,6 @@ constexpr int WT_HASH = 1024;    // hash slots per warp (power of two)
 constexpr int WT_QCAP = 512;     // largest IC set kept in the warp tier
 constexpr int LT_QCAP = 1024;    // largest LT walk kept in the warp tier
 constexpr int STAGE = 128;       // live candidates of one slab (32 lanes x 4 edges)
-constexpr int WARP_HEAVY_GROUPS = 4096;  // warp tiers hand samples meeting longer in-lists to the CTA tier
 constexpr int CTA_HEAVY_GROUPS = 512;    // the CTA tier splits longer in-lists over all its warps
 constexpr int CTA_HEAVY_CAP = 256;       // heavy in-lists per level shared this way
 
@@ -338,7 +337,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, WARP_HEAVY_GROUPS, known, visit, to_cta) == 2) {
+      if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) == 2) {
         handoff = true;
         break;
       }
