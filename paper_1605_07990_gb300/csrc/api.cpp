@@ -222,6 +222,10 @@ struct Sampler {
   int64_t fail_cap = 0, redo_cap = 0;
   uint32_t* slot_bitmap = nullptr;
   int32_t* slot_queue = nullptr;
+  int32_t* small_queue = nullptr;
+  uint32_t* small_bitmap = nullptr;
+  int64_t* big2_list = nullptr;
+  int64_t big2_cap = 0;
   uint8_t* hit = nullptr;
   int64_t hit_cap = 0;
   uint32_t* seed_bits = nullptr;
@@ -263,6 +267,9 @@ struct Sampler {
     if (!cfg.cta_smem_bitmap) {
       TRY(dev_alloc(&slot_bitmap, (size_t)words * (size_t)cfg.cta_blocks, X.st));
       CU(cudaMemsetAsync(slot_bitmap, 0, sizeof(uint32_t) * (size_t)words * (size_t)cfg.cta_blocks, X.st));
+      TRY(dev_alloc(&small_queue, (size_t)cfg.small_qcap * (size_t)cfg.small_blocks, X.st));
+      TRY(dev_alloc(&small_bitmap, (size_t)words * (size_t)cfg.small_blocks, X.st));
+      CU(cudaMemsetAsync(small_bitmap, 0, sizeof(uint32_t) * (size_t)words * (size_t)cfg.small_blocks, X.st));
     }
     TRY(dev_alloc(&seed_bits, (size_t)words, X.st));
     if (model == 0) {
@@ -296,6 +303,9 @@ struct Sampler {
     dev_free(redo_list, st);
     dev_free(slot_bitmap, st);
     dev_free(slot_queue, st);
+    dev_free(small_queue, st);
+    dev_free(small_bitmap, st);
+    dev_free(big2_list, st);
     dev_free(hit, st);
     dev_free(seed_bits, st);
     dev_free(bprefix, st);
@@ -319,6 +329,10 @@ struct Sampler {
     J.mid_slots = mid_slots;
     J.slot_bitmap = slot_bitmap;
     J.slot_queue = slot_queue;
+    J.small_qcap = cfg.small_qcap;
+    J.small_queue = small_queue;
+    J.small_bitmap = small_bitmap;
+    J.big2_list = big2_list;
     J.bitmap_words = (g.n + 31) / 32;
     J.ctr = d_ctr;
     J.fail_list = fail_list;
@@ -365,6 +379,7 @@ struct Sampler {
     const int64_t j0 = P.count;
     if (j0 + count > (int64_t)0x7FFFFFFF) return fail(SSA_E_POOL_FULL, "more than 2^31 RR sets");
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&big2_list, &big2_cap, count, 0, X.st));
     TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&fail_list, &fail_cap, count, 0, X.st));
     TRY(dev_grow(&redo_list, &redo_cap, count, 0, X.st));
@@ -448,6 +463,7 @@ struct Sampler {
   // Hit-test batch (Estimate-Inf): hit[i] = R_{j0+i} meets the seed bits.
   ssa_status hits(uint64_t seed, uint32_t stream, int64_t j0, int64_t count, Exec& X) {
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&big2_list, &big2_cap, count, 0, X.st));
     TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&hit, &hit_cap, count, 0, X.st));
     SampleJob J = job(seed, stream, j0, count);

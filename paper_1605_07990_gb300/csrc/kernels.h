@@ -25,6 +25,8 @@ struct Counters {
   unsigned long long mid_work;     // global warp tier: next list index
   unsigned long long big_count;    // samples handed to the CTA tier
   unsigned long long big_work;     // CTA tier: next list index
+  unsigned long long big2_count;   // samples that outgrew the small CTAs' queue
+  unsigned long long big2_work;
   unsigned long long cursor;       // pool entries reserved (absolute)
   unsigned long long edge_visits;  // in-edges examined
   unsigned long long node_visits;  // nodes added to RR sets
@@ -72,6 +74,11 @@ struct SampleJob {
   int64_t* big_list = nullptr;   // capacity `count`
   uint32_t* slot_bitmap = nullptr;  // per CTA slot: bitmap_words (unused when the bitmap is in smem)
   int32_t* slot_queue = nullptr;    // per CTA slot: n entries
+  // small CTAs (global bitmap only): per slot a queue of small_qcap entries and a bitmap
+  int small_qcap = 0;
+  int32_t* small_queue = nullptr;
+  uint32_t* small_bitmap = nullptr;
+  int64_t* big2_list = nullptr;     // capacity `count`
   int64_t bitmap_words = 0;
   Counters* ctr = nullptr;
 };
@@ -82,6 +89,8 @@ struct LaunchCfg {
   int cta_blocks = 0;    // grid of the CTA tier (= number of scratch slots)
   int mid_blocks = 0;    // grid of the global-memory warp tier
   int cta_threads = 1024;
+  int small_blocks = 0;  // small CTAs (256 threads) when the bitmap lives in global memory
+  int small_qcap = 0;
   bool cta_smem_bitmap = false;
   int64_t smem_bitmap_bytes = 0;
 };

@@ -15,6 +15,8 @@
 // (b) in the CTA tier skips the draw of a group whose live-able edges all
 // come from already-visited nodes (such an edge cannot change the set), and
 // (c) compacts the live candidates of a 128-edge slab into one insert round.
+#include <algorithm>
+
 #include "device.cuh"
 
 namespace ssa {
@@ -440,33 +442,43 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
 }
 
 // CTA tier: one CTA per large sample.
-template <int MODE, bool SMEM_BITMAP>
-__global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
+// KIND 0: the only CTA stage (bitmap in shared memory, queue of n entries).
+// KIND 1: small CTAs (bitmap in global memory, queue of small_qcap entries);
+//         a set that outgrows the queue goes on to KIND 2.
+// KIND 2: full-size CTAs (global bitmap, queue of n entries) for those sets.
+template <int MODE, bool SMEM_BITMAP, int KIND>
+__global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(SampleJob J) {
+  constexpr int WARPS = KIND == 1 ? 8 : 32;
   extern __shared__ __align__(16) uint32_t s_bits[];
   __shared__ long long s_item;
   __shared__ int s_tail, s_next, s_hit, s_ok;
   __shared__ unsigned long long s_pos;
-  __shared__ uint32_t s_stage[32][STAGE];
+  __shared__ uint32_t s_stage[WARPS][STAGE];
   // heavy in-lists of the current level, expanded by all warps together
   __shared__ uint32_t s_hlo[CTA_HEAVY_CAP], s_hhi[CTA_HEAVY_CAP];
   __shared__ int s_hpref[CTA_HEAVY_CAP];
   __shared__ int s_nheavy, s_htotal, s_hnext;
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
   const int64_t n = J.g.n;
-  uint32_t* bits = SMEM_BITMAP ? s_bits : J.slot_bitmap + (size_t)blockIdx.x * (size_t)J.bitmap_words;
-  int32_t* Q = J.slot_queue + (size_t)blockIdx.x * (size_t)n;
+  const int64_t qcap = KIND == 1 ? (int64_t)J.small_qcap : n;
+  uint32_t* bits = SMEM_BITMAP ? s_bits
+                   : (KIND == 1 ? J.small_bitmap : J.slot_bitmap) + (size_t)blockIdx.x * (size_t)J.bitmap_words;
+  int32_t* Q = (KIND == 1 ? J.small_queue : J.slot_queue) + (size_t)blockIdx.x * (size_t)qcap;
   uint32_t* stage = s_stage[tid >> 5];
   if (SMEM_BITMAP)
     for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
-  const long long big_count = (long long)*((volatile unsigned long long*)&J.ctr->big_count);
+  unsigned long long* work = KIND == 2 ? &J.ctr->big2_work : &J.ctr->big_work;
+  const int64_t* list = KIND == 2 ? J.big2_list : J.big_list;
+  const long long big_count =
+      (long long)*((volatile unsigned long long*)(KIND == 2 ? &J.ctr->big2_count : &J.ctr->big_count));
   unsigned long long ev = 0, nv = 0, dr = 0;
   __syncthreads();
   for (;;) {
-    if (tid == 0) s_item = (long long)atomicAdd(&J.ctr->big_work, 1ull);
+    if (tid == 0) s_item = (long long)atomicAdd(work, 1ull);
     __syncthreads();
     const long long item = s_item;
     if (item >= big_count) break;
-    const int64_t j = J.big_list[item];
+    const int64_t j = list[item];
     const int32_t root = pick_root(J, j);
     if (tid == 0) {
       bits[root >> 5] |= 1u << (root & 31);
@@ -477,10 +489,12 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
     __syncthreads();
     if (J.model == 0) {
       const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
-      // a stale 0 only costs a draw; bits are never cleared during a sample
-      auto known = [&](uint32_t u) {
-        const uint32_t w = SMEM_BITMAP ? bits[u >> 5] : __ldcg(bits + (u >> 5));
-        return (w >> (u & 31)) & 1u;
+      // a stale 0 only costs a draw; bits are never cleared during a sample.  With the
+      // bitmap in global memory the check would cost an L2 round trip per group, more
+      // than the draw it can save, so only the shared-memory bitmap is consulted.
+      auto known = [&](uint32_t u) -> bool {
+        if (!SMEM_BITMAP) return false;
+        return (bits[u >> 5] >> (u & 31)) & 1u;
       };
       auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
         bool is_new = false;
@@ -489,15 +503,17 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
           is_new = !(atomicOr(bits + (u >> 5), mask) & mask);
         }
         const unsigned m = __ballot_sync(FULL_MASK, is_new);
+        int base = 0;
         if (m) {
-          int base = 0;
           if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
           base = __shfl_sync(FULL_MASK, base, 0);
           if (is_new) {
-            Q[base + __popc(m & lt_mask)] = (int32_t)u;
+            const int pos = base + __popc(m & lt_mask);
+            if (KIND != 1 || pos < qcap) Q[pos] = (int32_t)u;
             if (MODE == MODE_HIT && test_bit(J.seed_bits, u)) s_hit = 1;
           }
         }
+        if (KIND == 1 && base + __popc(m) > qcap) return true;  // outgrew the small queue
         if (MODE == MODE_HIT) return __any_sync(FULL_MASK, *(volatile int*)&s_hit != 0);
         return false;
       };
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
       for (;;) {
         // every thread is past the previous barrier and nobody writes s_hit
         // until the next one, so this exit test is uniform across the CTA
-        if (lvl_begin >= lvl_end || s_hit) break;
+        if (lvl_begin >= lvl_end || s_hit || (KIND == 1 && s_tail > qcap)) break;
         if (tid == 0) s_next = lvl_begin;
         __syncthreads();
         for (;;) {
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
         }
         __syncthreads();
         const int nh = min(s_nheavy, CTA_HEAVY_CAP);
-        if (nh > 0 && !s_hit) {
+        if (nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
           // groups of the heavy in-lists, dealt to all warps 32 at a time
           if (wid == 0) {
             int carry = 0;
@@ -583,6 +599,10 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
         dr += 1;
         const uint32_t mask = 1u << (u & 31);
         if (bits[u >> 5] & mask) break;
+        if (KIND == 1 && tail >= qcap) {
+          tail = (int)qcap + 1;  // outgrew the small queue
+          break;
+        }
         bits[u >> 5] |= mask;
         Q[tail++] = u;
         if (MODE == MODE_HIT) hit = test_bit(J.seed_bits, (uint32_t)u);
@@ -593,6 +613,16 @@ __global__ void __launch_bounds__(1024, 1) k_sample_cta(SampleJob J) {
     }
     __syncthreads();
     const int tail = s_tail;
+    if (KIND == 1 && tail > qcap) {
+      // the set outgrew this stage's queue: full-size CTAs redo it; clear the whole bitmap
+      if (tid == 0) {
+        const unsigned long long b = atomicAdd(&J.ctr->big2_count, 1ull);
+        J.big2_list[b] = j;
+      }
+      for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
+      __syncthreads();
+      continue;
+    }
     if (MODE == MODE_STORE) {
       if (tid == 0) {
         unsigned long long pos = 0;
@@ -647,6 +677,15 @@ LaunchCfg sampler_config(const GraphView& g, int model) {
   c.cta_smem_bitmap = c.smem_bitmap_bytes <= SMEM_BITMAP_MAX_BYTES;
   c.cta_threads = 1024;
   c.cta_blocks = c.num_sms;
+  if (!c.cta_smem_bitmap) {
+    // global bitmap: many small CTAs first, a few full-size ones for the largest sets
+    int small_per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1>, 256, 0);
+    if (small_per_sm < 1) small_per_sm = 1;
+    c.small_blocks = c.num_sms * small_per_sm;
+    c.small_qcap = (int)std::min<int64_t>(g.n, 1 << 20);
+    c.cta_blocks = std::max(8, c.num_sms / 4);
+  }
   c.mid_blocks = c.num_sms * 2;  // 16 warps per SM, each with its own global hash and queue
   return c;
 }
@@ -659,7 +698,7 @@ size_t mid_queue_per_warp() { return MID_QSLOTS; }
 size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c) {
   const size_t words = (size_t)((g.n + 31) / 32);
   size_t per_slot = (size_t)g.n * 4 + (c.cta_smem_bitmap ? 0 : words * 4);
-  return per_slot * (size_t)c.cta_blocks;
+  return per_slot * (size_t)c.cta_blocks + ((size_t)c.small_qcap * 4 + words * 4) * (size_t)c.small_blocks;
 }
 
 cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
@@ -681,13 +720,16 @@ cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStrea
 
 template <int MODE, bool SB>
 static cudaError_t launch_cta_t(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
-  const size_t smem = SB ? (size_t)c.smem_bitmap_bytes : 0;
   if (SB) {
-    cudaError_t e = cudaFuncSetAttribute(k_sample_cta<MODE, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = (size_t)c.smem_bitmap_bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_sample_cta<MODE, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    k_sample_cta<MODE, true, 0><<<c.cta_blocks, c.cta_threads, smem, st>>>(J);
+  } else {
+    k_sample_cta<MODE, false, 1><<<c.small_blocks, 256, 0, st>>>(J);
+    k_sample_cta<MODE, false, 2><<<c.cta_blocks, c.cta_threads, 0, st>>>(J);
   }
-  k_sample_cta<MODE, SB><<<c.cta_blocks, c.cta_threads, smem, st>>>(J);
   return cudaGetLastError();
 }
 

@@ -222,3 +222,23 @@ def test_autotune_picks_a_candidate():
     r = P.ssa_solve(gg, 1, 0, 10, 0.1, 1.0 / el.n, 3)
     assert r.mid_cap == cap
     assert P.ssa_autotune(gg, P.SSA_LT)[0] == 0
+
+
+def test_global_bitmap_ctas_and_queue_overflow():
+    # n = 2^22: the CTA tier's bitmap lives in global memory (small CTAs first, full-size ones for sets
+    # that outgrow the 2^20-entry small queue); with every edge live the sets are whole ancestor sets
+    el = inputs.rmat(22, 1 << 25, seed=9)
+    thr = np.full(el.m, 0xFFFFFFFF, np.uint32)
+    og, gg = _pair(el, oracle.W_EXPLICIT, thr)
+    P.ssa_set_tuning(gg, 0, 64)  # long in-lists go to the CTA tier at once
+    op, gp = _check_pool(og, gg, oracle.IC, seed=2, stream=0, N=24)
+    off, _ = op.arrays()
+    assert np.diff(off).max() > (1 << 20)  # the full-size stage was needed
+    seeds, _, _ = op.max_coverage(24, 3)
+    assert P.ssa_estimate_inf(gg, oracle.IC, 2, 1, seeds, 10.5, 200) == \
+        oracle.estimate_inf(og, oracle.IC, 2, 1, seeds, 10.5, 200)[:2]
+    # trivalency at the same size: mostly small sets through every stage
+    og2, gg2 = _pair(el, oracle.W_TRIVALENCY)
+    for mid, heavy in ((0, 64), (16384, 0x7FFFFFFF)):
+        P.ssa_set_tuning(gg2, mid, heavy)
+        _check_pool(og2, gg2, oracle.IC, seed=3, stream=0, N=2000)
