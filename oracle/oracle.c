@@ -90,6 +90,7 @@ typedef struct {
   int64_t* off;  /* n+1 */
   int32_t* src;  /* m: tail u of in-edge (u,v) */
   uint32_t* thr; /* m: live iff draw < thr, or thr == 0xFFFFFFFF */
+  int weighting; /* W_WC, W_TRIVALENCY or W_EXPLICIT */
 } orc_graph;
 
 enum { W_WC = 0, W_TRIVALENCY = 1, W_EXPLICIT = 2 };
@@ -111,7 +112,7 @@ orc_graph* orc_graph_build(int64_t n, int64_t m, const int32_t* src, const int32
     if (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n) return NULL;
   if (weighting == W_EXPLICIT && m > 0 && !thr_in) return NULL;
   orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
-  g->n = n; g->m = m;
+  g->n = n; g->m = m; g->weighting = weighting;
   g->off = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
   g->src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m ? m : 1));
   g->thr = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
@@ -234,16 +235,30 @@ static int64_t rr_set(orc_sampler* s, uint32_t stream, uint64_t j, int32_t* out)
       }
     }
   } else {
-    /* LT live-edge world: node v keeps the in-edge of index floor(r*d_in/2^32),
-     * each with probability 1/d_in; the RR set follows kept edges backwards
-     * from the source until a node with no in-edge or an already-seen node. */
+    /* LT live-edge world: node v keeps at most one in-edge.  Weighted cascade
+     * (w = 1/d_in): the edge of index floor(r*d_in/2^32), each with probability
+     * 1/d_in.  General weights (explicit thresholds t_e = w * 2^32, sum <= 2^32):
+     * the first in-edge e with r < t_1 + ... + t_e, none when r is past the
+     * sum (probability 1 - sum of w).  The RR set follows kept edges backwards
+     * from the source until a node with no kept edge or an already-seen node. */
     int32_t v = root;
     for (;;) {
       int64_t d = g->off[v + 1] - g->off[v];
       if (d == 0) break;
       uint32_t r[4];
       keyed(s->seed, P_LT, stream, j, (uint64_t)v, r);
-      int32_t u = g->src[g->off[v] + mulhi32(r[0], (uint32_t)d)];
+      int64_t pick = -1;
+      if (g->weighting == W_EXPLICIT) {
+        uint64_t cum = 0;
+        for (int64_t e = g->off[v]; e < g->off[v + 1]; ++e) {
+          cum += g->thr[e];
+          if ((uint64_t)r[0] < cum) { pick = e; break; }
+        }
+      } else {
+        pick = g->off[v] + mulhi32(r[0], (uint32_t)d);
+      }
+      if (pick < 0) break;
+      int32_t u = g->src[pick];
       s->edge_visits++;
       if (s->visited[u]) break;
       s->visited[u] = 1;

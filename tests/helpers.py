@@ -137,3 +137,23 @@ def ancestors(n, src, dst, root):
                 seen.add(u)
                 stack.append(u)
     return seen
+
+
+def exact_influence_lt_general(n, src, dst, thr, S):
+    """I(S) under LT with general in-weights w_e = thr_e / 2^32 (sum <= 1 per node):
+    every node keeps in-edge e with probability w_e, or none with the rest."""
+    ins = [[] for _ in range(n)]
+    for e in range(len(src)):
+        ins[int(dst[e])].append((int(src[e]), int(thr[e]) / U32))
+    choices = [lst + [(None, 1.0 - sum(w for _, w in lst))] for lst in ins]
+    total = 0.0
+    for pick in itertools.product(*choices):
+        pr = 1.0
+        live = []
+        for v, (u, w) in enumerate(pick):
+            pr *= w
+            if u is not None:
+                live.append((u, v))
+        if pr > 0.0:
+            total += pr * len(reach_forward(n, live, S))
+    return total

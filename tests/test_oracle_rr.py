@@ -142,3 +142,29 @@ def test_keyed_independence_of_order(orc):
         assert np.array_equal(orc.rr_set(g, orc.IC, 99, 3, j), sets[j])
     other = orc.Pool(g, orc.IC, seed=99, stream=4).grow(50).sets()
     assert any(not np.array_equal(a, b) for a, b in zip(sets, other))
+
+
+@pytest.mark.parametrize("gi", [0, 1])
+def test_lt_general_weights_lemma1(orc, gi):
+    # LT with explicit in-weights summing to at most 1 (Sec. 2.1): exact enumeration vs RIS estimate
+    from helpers import exact_influence_lt_general
+    el = list(_tiny_graphs())[gi]
+    rng = np.random.default_rng(40 + gi)
+    d = np.bincount(el.dst, minlength=el.n)
+    # random weights per in-edge scaled so each node's in-weights sum to a random value <= 1
+    w = rng.uniform(0.2, 1.0, el.m)
+    tot = np.zeros(el.n)
+    np.add.at(tot, el.dst, w)
+    scale = rng.uniform(0.5, 1.0, el.n) / np.maximum(tot, 1e-9)
+    thr = np.floor(w * scale[el.dst] * 2**32).astype(np.uint64)
+    thr = np.minimum(thr, 2**32 - 1).astype(np.uint32)
+    g = orc.Graph.from_edges(el, orc.W_EXPLICIT, thr=thr)
+    off, src, t2 = g.csr()
+    dst = np.repeat(np.arange(el.n), np.diff(off))
+    N = 200_000
+    p = orc.Pool(g, orc.LT, seed=29).grow(N)
+    for S in ([0], [3], [1, 4]):
+        I = exact_influence_lt_general(el.n, src, dst, t2, S)
+        est = p.coverage(0, N, S) / N
+        assert within_chernoff(est, I / el.n, N), (S, I, est * el.n)
+    assert d.sum() == el.m
