@@ -59,8 +59,12 @@ typedef enum { SSA_ALGO_SSA = 0, SSA_ALGO_DSSA = 1 } ssa_algo;
  *                     WEIGHT draw of the edge's CSR position: index floor(3 r / 2^32),
  *                     t = floor(2^32 w) = 429496729, 42949672, 4294967
  *   SSA_W_EXPLICIT    t given per input edge
- * LT (Sec. 2.1) needs SSA_W_WC: each visited node keeps the in-edge of index
- * floor(r d_in / 2^32) of its in-list, r its keyed LT draw. */
+ * LT (Sec. 2.1) in its live-edge form: each visited node keeps at most one
+ * in-edge, chosen by its keyed LT draw r.  SSA_W_WC: the in-edge of index
+ * floor(r d_in / 2^32) of its in-list (w = 1/d_in).  SSA_W_EXPLICIT: t_e are
+ * the in-weights times 2^32 and must sum to at most 2^32 per node; the kept
+ * edge is the first e of the in-list with r < t_1 + ... + t_e, none when r is
+ * past the sum (probability 1 - sum of w).  SSA_W_TRIVALENCY is IC only. */
 typedef enum { SSA_W_WC = 0, SSA_W_TRIVALENCY = 1, SSA_W_EXPLICIT = 2 } ssa_weighting;
 
 typedef struct ssa_graph ssa_graph;

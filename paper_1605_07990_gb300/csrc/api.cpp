@@ -231,6 +231,7 @@ struct Sampler {
   uint32_t* seed_bits = nullptr;
   uint64_t* bprefix = nullptr;
   uint64_t wsum = 0;
+  int lt_cumulative = 0;
   int mid_cap = 16384;  // IC: largest set the global warp tier keeps (0 = none)
   int heavy_groups = 0x7FFFFFFF;  // IC: warp tiers hand samples with longer in-lists to the CTA tier
   int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
@@ -251,6 +252,7 @@ struct Sampler {
   ssa_status init(const ssa_graph* G, int mdl, const uint32_t* benefit, Exec& X) {
     g = G->view();
     model = mdl;
+    lt_cumulative = (mdl == 1 && G->weighting == SSA_W_EXPLICIT) ? 1 : 0;
     {
       std::lock_guard<std::mutex> lock(G->tune_mu);
       if (G->tuned_mid_cap >= 0) {
@@ -315,6 +317,7 @@ struct Sampler {
     SampleJob J;
     J.g = g;
     J.model = model;
+    J.lt_cumulative = lt_cumulative;
     J.seed = seed;
     J.stream = stream;
     J.j0 = j0;
@@ -879,8 +882,8 @@ ssa_status check_params(const ssa_graph* g, const ssa_params* p) {
   if (!(p->delta > 0.0 && p->delta < 1.0)) return fail(SSA_E_ARG, "delta must lie in (0, 1)");
   if (p->model != SSA_IC && p->model != SSA_LT) return fail(SSA_E_ARG, "unknown model");
   if (p->algo != SSA_ALGO_SSA && p->algo != SSA_ALGO_DSSA) return fail(SSA_E_ARG, "unknown algorithm");
-  if (p->model == SSA_LT && g->weighting != SSA_W_WC)
-    return fail(SSA_E_ARG, "LT needs weighted-cascade in-weights (SSA_W_WC)");
+  if (p->model == SSA_LT && g->weighting == SSA_W_TRIVALENCY)
+    return fail(SSA_E_ARG, "LT needs in-weights that sum to at most 1: SSA_W_WC or SSA_W_EXPLICIT");
   return SSA_OK;
 }
 
@@ -1266,7 +1269,8 @@ ssa_status ssa_pool_create(const ssa_graph* g, ssa_model model, uint64_t seed, u
                            const uint32_t* benefit, ssa_pool** out) {
   if (!g || !out) return fail(SSA_E_ARG, "null graph or output");
   if (model != SSA_IC && model != SSA_LT) return fail(SSA_E_ARG, "unknown model");
-  if (model == SSA_LT && g->weighting != SSA_W_WC) return fail(SSA_E_ARG, "LT needs SSA_W_WC");
+  if (model == SSA_LT && g->weighting == SSA_W_TRIVALENCY)
+    return fail(SSA_E_ARG, "LT needs SSA_W_WC or SSA_W_EXPLICIT in-weights");
   if (stream > 255) return fail(SSA_E_ARG, "stream must be < 256");
   ssa_pool* p = new ssa_pool();
   p->g = g;

@@ -44,6 +44,7 @@ enum : int { MODE_STORE = 0, MODE_HIT = 1 };
 struct SampleJob {
   GraphView g;
   int model = 0;                 // 0 IC, 1 LT
+  int lt_cumulative = 0;         // LT with explicit in-weights: pick by running threshold sums
   uint64_t seed = 0;
   uint32_t stream = 0;
   int64_t j0 = 0, count = 0;     // samples [j0, j0+count), or work_list[0, count)

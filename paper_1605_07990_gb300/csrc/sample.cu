@@ -407,7 +407,31 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
       const int64_t d = hi - lo;
       if (d == 0) break;
       const uint4 r = philox_x((uint32_t)cur, sc, J.rk);
-      const int32_t u = (int32_t)__ldg(&J.g.edge[lo + __umulhi(r.x, (uint32_t)d)].x);
+      int64_t pick;
+      if (!J.lt_cumulative) {
+        pick = lo + __umulhi(r.x, (uint32_t)d);  // w = 1/d_in: one of the d in-edges
+      } else {
+        // general in-weights: first in-edge whose running threshold sum passes r, or none
+        pick = -1;
+        unsigned long long carry = 0;
+        for (int64_t b = lo; b < hi; b += 32) {
+          const int64_t e = b + lane;
+          unsigned long long incl = e < hi ? (unsigned long long)__ldg(&J.g.edge[e].y) : 0ull;
+#pragma unroll
+          for (int dd = 1; dd < 32; dd <<= 1) {
+            const unsigned long long t = __shfl_up_sync(FULL_MASK, incl, dd);
+            if (lane >= dd) incl += t;
+          }
+          const unsigned hitm = __ballot_sync(FULL_MASK, e < hi && (unsigned long long)r.x < carry + incl);
+          if (hitm) {
+            pick = b + __ffs(hitm) - 1;
+            break;
+          }
+          carry += __shfl_sync(FULL_MASK, incl, 31);
+        }
+        if (pick < 0) break;  // no in-edge kept: the walk ends here
+      }
+      const int32_t u = (int32_t)__ldg(&J.g.edge[pick].x);
       if (lane == 0) {
         ev += 1;
         dr += 1;
@@ -594,7 +618,21 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
         const int64_t lo = J.g.off[cur], hi = J.g.off[cur + 1];
         if (hi == lo) break;
         const uint4 r = philox_x((uint32_t)cur, sc, J.rk);
-        const int32_t u = (int32_t)J.g.edge[lo + __umulhi(r.x, (uint32_t)(hi - lo))].x;
+        int64_t pick = -1;
+        if (!J.lt_cumulative) {
+          pick = lo + __umulhi(r.x, (uint32_t)(hi - lo));
+        } else {
+          unsigned long long cum = 0;
+          for (int64_t e = lo; e < hi; ++e) {
+            cum += J.g.edge[e].y;
+            if ((unsigned long long)r.x < cum) {
+              pick = e;
+              break;
+            }
+          }
+          if (pick < 0) break;
+        }
+        const int32_t u = (int32_t)J.g.edge[pick].x;
         ev += 1;
         dr += 1;
         const uint32_t mask = 1u << (u & 31);

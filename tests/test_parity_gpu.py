@@ -242,3 +242,22 @@ def test_global_bitmap_ctas_and_queue_overflow():
     for mid, heavy in ((0, 64), (16384, 0x7FFFFFFF)):
         P.ssa_set_tuning(gg2, mid, heavy)
         _check_pool(og2, gg2, oracle.IC, seed=3, stream=0, N=2000)
+
+
+def test_lt_general_weights():
+    # LT with explicit in-weights (sums <= 1, some nodes with slack): sets, greedy and full solves
+    el = inputs.rmat(13, 1 << 16, seed=12)
+    rng = np.random.default_rng(4)
+    w = rng.uniform(0.1, 1.0, el.m)
+    tot = np.zeros(el.n)
+    np.add.at(tot, el.dst, w)
+    frac = rng.uniform(0.6, 1.0, el.n)
+    thr = np.minimum(np.floor(w * (frac / np.maximum(tot, 1e-12))[el.dst] * 2**32), 2**32 - 1).astype(np.uint32)
+    og, gg = _pair(el, oracle.W_EXPLICIT, thr)
+    op, gp = _check_pool(og, gg, oracle.LT, seed=6, stream=0, N=5000)
+    a = op.max_coverage(5000, 30)
+    b = gp.max_coverage(5000, 30)
+    assert np.array_equal(a[0], b[0]) and a[2] == b[2]
+    for algo in (0, 1):
+        _same_solution(oracle.solve(og, algo, oracle.LT, 20, 0.1, 1.0 / el.n, 2),
+                       P.ssa_solve(gg, algo, oracle.LT, 20, 0.1, 1.0 / el.n, 2))
