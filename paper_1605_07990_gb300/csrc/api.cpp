@@ -508,6 +508,8 @@ struct Cover {
   unsigned int* sync = nullptr;
   unsigned long long* chunk_q = nullptr;
   int64_t chunk_cap = 0;
+  unsigned int* hist = nullptr;   // greedy gain histograms (2 x 4096) and cache counts (2), one buffer
+  int32_t* cache = nullptr;       // greedy candidate caches (2 x 8192)
   int32_t* d_seeds = nullptr;
   int32_t* d_gains = nullptr;
   int k_cap = 0;
@@ -531,6 +533,8 @@ struct Cover {
     partial_cap = X.num_sms * 8;
     TRY(dev_alloc(&partial, (size_t)partial_cap, X.st));
     TRY(dev_alloc(&sync, 128, X.st));
+    TRY(dev_alloc(&hist, 2 * 4096 + 2, X.st));
+    TRY(dev_alloc(&cache, 2 * 8192, X.st));
     TRY(dev_alloc(&d_count, 1, X.st));
     TRY(dev_alloc(&d_first, 2, X.st));
     return SSA_OK;
@@ -554,6 +558,8 @@ struct Cover {
     dev_free(partial, st);
     dev_free(sync, st);
     dev_free(chunk_q, st);
+    dev_free(hist, st);
+    dev_free(cache, st);
     dev_free(d_seeds, st);
     dev_free(d_gains, st);
     dev_free(d_count, st);
@@ -639,6 +645,7 @@ struct Cover {
     int h = X.begin(SSA_K_GREEDY);
     CU(cudaMemsetAsync(covered, 0, (size_t)std::max<int64_t>(N, 1), X.st));
     CU(cudaMemsetAsync(sync, 0, sizeof(unsigned int) * 128, X.st));
+    CU(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * (2 * 4096 + 2), X.st));
     // padding nodes can never be picked
     if (n_pad > n) CU(cudaMemsetAsync(cnt + n, 0xC0, sizeof(int32_t) * (size_t)(n_pad - n), X.st));
     GreedyJob J{};
@@ -659,6 +666,9 @@ struct Cover {
     J.sync = sync;
     J.chunk_q = chunk_q;
     J.chunk_cap = chunk_cap;
+    J.hist = hist;
+    J.cache = cache;
+    J.cache_n = hist + 2 * 4096;
     int blocks = 0;
     // one cooperative greedy grid on the device at a time (solvers on other
     // host threads, e.g. serving slots, wait here)

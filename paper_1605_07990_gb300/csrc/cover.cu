@@ -142,44 +142,55 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
   return x;
 }
 
-// Persistent greedy: all k picks of Algorithm 2 in one cooperative launch.
-// Per pick: every block scans its slice of the gains for the packed max key
-// (largest gain, then smallest id; picked nodes hold a negative gain), a grid
-// barrier, every block reduces the per-block partials to the same (v*, gain),
-// then warps walk v*'s inverted lists of all index batches and, for each
-// newly covered set, decrement the gains of its members; a second barrier
-// closes the pick.  Barrier waits are bounded: on a timeout the kernel sets
-// sync[2] and every block returns.
 // sync layout: arrival count, generation and timeout flag on separate
 // 128-byte lines so that polling does not contend with the arrivals.
 constexpr int SYNC_COUNT = 0, SYNC_GEN = 32, SYNC_ERR = 64, SYNC_CHUNKS = 96, SYNC_WORDS = 128;
 constexpr int DEC_CHUNK = 2048;  // covered sets longer than this are decremented in chunks by all warps
+constexpr int CACHE_MAX = 8192;  // greedy candidate cache entries
+constexpr int HBINS = 4096;      // gain histogram: gain g >= 1 counts in bin min(g, HBINS - 1)
 
-__device__ __forceinline__ bool grid_barrier(unsigned int* sync) {
+// Grid barrier for a cooperative launch.  The generation word and a 32-bit
+// value published by the last block to arrive share one 64-bit word, so a
+// waiter learns both from the poll that releases it: with `publish` given,
+// *info receives *publish as it stood after every block's writes before the
+// barrier.  A wait gives up after ~seconds, sets sync[SYNC_ERR] and returns
+// false; that block then leaves the kernel, and the others give up at their
+// next barrier, since it never arrives.
+__device__ __forceinline__ bool grid_barrier(unsigned int* sync, const unsigned int* publish = nullptr,
+                                             unsigned int* info = nullptr) {
+  __shared__ unsigned int s_info, s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = sync + SYNC_GEN;
-    const unsigned int g = *gen;
+    volatile unsigned long long* gw = reinterpret_cast<volatile unsigned long long*>(sync + SYNC_GEN);
+    const unsigned int g = (unsigned int)*gw;
+    unsigned int got = 0, ok = 1;
     __threadfence();
     if (atomicAdd(sync + SYNC_COUNT, 1u) + 1u == gridDim.x) {
       atomicExch(sync + SYNC_COUNT, 0u);
       __threadfence();
-      atomicAdd(sync + SYNC_GEN, 1u);
+      if (publish) got = *(volatile const unsigned int*)publish;
+      atomicExch((unsigned long long*)gw, ((unsigned long long)got << 32) | (unsigned long long)(g + 1u));
     } else {
       unsigned int ns = 8;
-      for (long long spins = 0; *gen == g; ++spins) {
+      unsigned long long w;
+      for (long long spins = 0; (unsigned int)(w = *gw) == g; ++spins) {
         if (spins > (1ll << 22)) {  // seconds: a barrier never takes that long
           atomicExch(sync + SYNC_ERR, 1u);
+          ok = 0;
           break;
         }
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
       }
+      got = (unsigned int)(w >> 32);
     }
     __threadfence();
+    s_info = got;
+    s_ok = ok;
   }
   __syncthreads();
-  return *((volatile unsigned int*)(sync + SYNC_ERR)) == 0u;
+  if (info) *info = s_info;
+  return s_ok != 0u;
 }
 
 __device__ __forceinline__ unsigned long long gain_key(int32_t c, uint32_t v) {
@@ -199,36 +210,207 @@ __device__ __forceinline__ void decrement_members(int32_t* cnt, const int32_t* m
   for (; t < len; t += 32) atomicSub(cnt + __ldg(mem + t), 1);
 }
 
+// Persistent greedy: all k picks of Algorithm 2 in one cooperative launch.
+//
+// Argmax.  A pick needs the node of largest gain, then smallest id (picked
+// nodes hold a negative gain); blocks write per-block maxima of packed keys,
+// meet at a grid barrier and all reduce the same partials.  Gains only fall,
+// so after a scan of all n nodes that finds the threshold g* with at most
+// CACHE_MAX nodes of gain >= g*, those nodes form a candidate cache: while the
+// best cached gain is still >= g*, it beats every node outside (all <= g* - 1,
+// ties included), and the pick scans the cache instead of all n nodes.  When
+// the best cached gain falls below g*, the pick scans all n nodes and builds
+// a new cache from a gain histogram taken in the same pass.
+//
+// Cover.  Warps walk v*'s inverted lists of all index batches and, for each
+// newly covered set, decrement the gains of its members; sets longer than
+// DEC_CHUNK are split into chunks queued for every warp after the barrier
+// that closes the pick.  Barrier waits are bounded (sync[SYNC_ERR] on timeout).
 __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   __shared__ unsigned long long s_red[32];
   __shared__ int64_t s_lo[GREEDY_MAX_LISTS], s_hi[GREEDY_MAX_LISTS];
+  __shared__ unsigned int s_hist[HBINS];
+  __shared__ long long s_scan[32], s_scan_tot;
   const int lane = threadIdx.x & 31;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t warp = gtid >> 5, nwarps = gthreads >> 5;
   const int64_t n4 = J.n_pad >> 2;
   const int4* c4 = reinterpret_cast<const int4*>(J.cnt);
+  // partials: [0, grid) for cache scans, [grid, 2 grid) for full scans, so a
+  // full scan after a missed cache never overwrites partials still being read
+  unsigned long long* part_full = J.partial + gridDim.x;
+  // Rebuild policy (every block tracks the same values): the first pick only
+  // scans; a rebuild needs at least REBUILD_MIN picks left; a cache that served
+  // fewer than REBUILD_MIN picks, or a rebuild that found no threshold,
+  // postpones the next rebuild by a doubling back-off.
+  constexpr int REBUILD_MIN = 8;
+  int rebuilds = 0, next_try = 1, backoff = REBUILD_MIN, built_at = 0, gstar = 0, g_prev = 0;
+  bool cached = false, stage = false;
+  int my_nc = 0;
+  // a block's cache slice, at most ceil(CACHE_MAX / grid) <= HBINS entries,
+  // shares the histogram's space: a histogram is only taken after a cache miss
+  int32_t* s_cand = reinterpret_cast<int32_t*>(s_hist);
   for (int i = 0; i < J.k; ++i) {
     unsigned long long best = 0;
-    for (int64_t q = gtid; q < n4; q += gthreads) {
-      const int4 c = __ldcg(c4 + q);
-      const uint32_t v = (uint32_t)(q * 4);
-      unsigned long long key;
-      key = gain_key(c.x, v);     best = key > best ? key : best;
-      key = gain_key(c.y, v + 1); best = key > best ? key : best;
-      key = gain_key(c.z, v + 2); best = key > best ? key : best;
-      key = gain_key(c.w, v + 3); best = key > best ? key : best;
+    bool have = false;
+    if (cached) {
+      if (stage) {
+        // first pick on a new cache: this block's slice (entries blockIdx.x +
+        // s * grid) moves to shared memory, so later picks gather only gains
+        const int cb = (rebuilds - 1) & 1;
+        const unsigned int nc = __ldcg(J.cache_n + cb);
+        my_nc = -1;
+        if (nc <= (unsigned int)CACHE_MAX) {
+          const int32_t* cache = J.cache + (size_t)cb * CACHE_MAX;
+          my_nc = nc > blockIdx.x ? (int)((nc - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+          for (int t = threadIdx.x; t < my_nc; t += blockDim.x) s_cand[t] = __ldcg(cache + blockIdx.x + (size_t)t * gridDim.x);
+        }
+        __syncthreads();
+        stage = false;
+      }
+      if (my_nc >= 0) {
+        for (int t = threadIdx.x; t < my_nc; t += blockDim.x) {
+          const int32_t v = s_cand[t];
+          const unsigned long long key = gain_key(__ldcg(J.cnt + v), (uint32_t)v);
+          best = key > best ? key : best;
+        }
+        best = block_max(best, s_red);
+        if (threadIdx.x == 0) J.partial[blockIdx.x] = best;
+        if (!grid_barrier(J.sync)) return;
+        best = 0;
+        for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
+          const unsigned long long key = __ldcg(J.partial + t);
+          best = key > best ? key : best;
+        }
+        best = block_max(best, s_red);
+        // every block reduced the same partials, so all take the same branch
+        have = best != 0 && (int)((uint32_t)(best >> 32) - 1u) >= gstar;
+      }
+      if (!have) {
+        cached = false;
+        if (i - built_at < REBUILD_MIN) {
+          next_try = i + backoff;
+          backoff = min(2 * backoff, 512);
+        } else {
+          backoff = REBUILD_MIN;
+        }
+      }
     }
-    best = block_max(best, s_red);
-    if (threadIdx.x == 0) J.partial[blockIdx.x] = best;
-    if (!grid_barrier(J.sync)) return;
-    best = 0;
-    for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
-      const unsigned long long key = __ldcg(J.partial + t);
-      best = key > best ? key : best;
+    if (!have) {
+      const bool rebuild = i >= next_try && J.k - i >= REBUILD_MIN;
+      // the histogram counts gains >= floor only (bin c - floor, the top bin
+      // "at least"): the cache threshold sits near the top, and low gains,
+      // the bulk of the nodes, would only contend on a few bins
+      const int floor_g = max(1, g_prev >> 2);
+      const int hb = rebuilds & 1;
+      if (rebuild) {
+        for (int t = threadIdx.x; t < HBINS; t += blockDim.x) s_hist[t] = 0u;
+        __syncthreads();
+      }
+      best = 0;
+      for (int64_t q = gtid; q < n4; q += gthreads) {
+        const int4 c = __ldcg(c4 + q);
+        const uint32_t v = (uint32_t)(q * 4);
+        unsigned long long key;
+        key = gain_key(c.x, v);     best = key > best ? key : best;
+        key = gain_key(c.y, v + 1); best = key > best ? key : best;
+        key = gain_key(c.z, v + 2); best = key > best ? key : best;
+        key = gain_key(c.w, v + 3); best = key > best ? key : best;
+        if (rebuild) {
+          if (c.x >= floor_g) atomicAdd(s_hist + min(c.x - floor_g, HBINS - 1), 1u);
+          if (c.y >= floor_g) atomicAdd(s_hist + min(c.y - floor_g, HBINS - 1), 1u);
+          if (c.z >= floor_g) atomicAdd(s_hist + min(c.z - floor_g, HBINS - 1), 1u);
+          if (c.w >= floor_g) atomicAdd(s_hist + min(c.w - floor_g, HBINS - 1), 1u);
+        }
+      }
+      best = block_max(best, s_red);
+      if (threadIdx.x == 0) part_full[blockIdx.x] = best;
+      if (rebuild) {
+        unsigned int* h = J.hist + (size_t)hb * HBINS;
+        for (int t = threadIdx.x; t < HBINS; t += blockDim.x)
+          if (s_hist[t]) atomicAdd(h + t, s_hist[t]);
+      }
+      if (!grid_barrier(J.sync)) return;
+      best = 0;
+      for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
+        const unsigned long long key = __ldcg(part_full + t);
+        best = key > best ? key : best;
+      }
+      best = block_max(best, s_red);
+      if (rebuild) {
+        // g* = floor + the smallest bin b with at most CACHE_MAX nodes in
+        // bins >= b: a descending block scan of the merged histogram (thread t
+        // holds bins HBINS-1-PER*t down to HBINS-PER*(t+1)); none when the
+        // top bin alone holds too many nodes
+        constexpr int PER = HBINS / 1024;
+        const unsigned int* h = J.hist + (size_t)hb * HBINS;
+        const int top = HBINS - 1 - (int)threadIdx.x * PER;
+        unsigned int hv[PER];
+        long long mine = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          hv[u] = __ldcg(h + top - u);
+          mine += hv[u];
+        }
+        long long above = block_exclusive_scan<long long>(mine, s_scan, &s_scan_tot);
+        unsigned long long key = 0;  // HBINS - b of the smallest qualifying bin
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          above += hv[u];
+          if (above <= (long long)CACHE_MAX) key = (unsigned long long)(HBINS - (top - u));
+        }
+        key = block_max(key, s_red);
+        int g = key ? floor_g + (HBINS - (int)key) : 0;
+        // a threshold above the best gain would leave the best node outside
+        if (g > (int)((uint32_t)(best >> 32) - 1u)) g = 0;
+        if (g > 0) {
+          // Some blocks may already be covering for this pick, so a gain read
+          // here may have fallen since the scan: below g* it stays below for
+          // good; at or above g* it was counted in the histogram, which bounds
+          // the cache at CACHE_MAX entries.
+          const int32_t vstar = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
+          unsigned int* nout = J.cache_n + hb;
+          int32_t* out = J.cache + (size_t)hb * CACHE_MAX;
+          // warp-uniform trip count, so the ballots below see all 32 lanes
+          for (int64_t q0 = gtid - lane; q0 < n4; q0 += gthreads) {
+            const int64_t q = q0 + lane;
+            int4 c = make_int4(-1, -1, -1, -1);
+            if (q < n4) c = __ldcg(c4 + q);
+            const int32_t v = (int32_t)(q * 4);
+            const int32_t cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const bool take = cv[u] >= g && v + u != vstar;
+              const unsigned int m = __ballot_sync(FULL_MASK, take);
+              if (m == 0u) continue;
+              const int leader = __ffs(m) - 1;
+              unsigned int at = 0;
+              if (lane == leader) at = atomicAdd(nout, (unsigned int)__popc(m));
+              at = __shfl_sync(FULL_MASK, at, leader) + (unsigned int)__popc(m & ((1u << lane) - 1u));
+              if (take && at < (unsigned int)CACHE_MAX) out[at] = v + u;
+            }
+          }
+          gstar = g;
+          cached = true;
+          built_at = i;
+          stage = true;
+        } else {
+          next_try = i + backoff;  // the top is too flat: full scans for a while
+          backoff = min(2 * backoff, 512);
+        }
+        // this parity's histogram and cache stay read-only until the next
+        // rebuild, which uses the other parity: clear that one now (nobody
+        // reads it any more: the last cache scan of it ended at the barrier above)
+        if (blockIdx.x == 0) {
+          for (int t = threadIdx.x; t < HBINS; t += blockDim.x) J.hist[(size_t)(hb ^ 1) * HBINS + t] = 0u;
+          if (threadIdx.x == 0) J.cache_n[hb ^ 1] = 0u;
+        }
+        rebuilds += 1;
+      }
     }
-    best = block_max(best, s_red);
     const int32_t vstar = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
+    g_prev = (int)((uint32_t)(best >> 32) - 1u);
     if (threadIdx.x < J.nlists) {
       s_lo[threadIdx.x] = J.lists[threadIdx.x].off[vstar];
       s_hi[threadIdx.x] = J.lists[threadIdx.x].off[vstar + 1];
@@ -243,10 +425,13 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
       const int32_t* samp = J.lists[b].samp;
       for (int64_t q = s_lo[b] + warp; q < s_hi[b]; q += nwarps) {
         const int32_t j = samp[q];
-        if (__ldcg(J.covered + j)) continue;
+        // the set's extent loads alongside its covered flag (one round trip, not two)
+        const uint8_t was = __ldcg(J.covered + j);
+        const int32_t len = J.set_len[j];
+        const int64_t start = J.set_start[j];
+        if (was) continue;
         __syncwarp();
         if (lane == 0) J.covered[j] = 1;
-        const int32_t len = J.set_len[j];
         int32_t mine = len;
         if (len > DEC_CHUNK) {
           // keep the first chunk, queue the rest for every warp after the barrier
@@ -258,15 +443,15 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
           for (int c = lane; c < nq; c += 32)
             J.chunk_q[at + c] = ((unsigned long long)(uint32_t)j << 32) | (uint32_t)((c + 1) * DEC_CHUNK);
         }
-        decrement_members(J.cnt, J.pool_nodes + J.set_start[j], mine, lane);
+        decrement_members(J.cnt, J.pool_nodes + start, mine, lane);
       }
     }
     // v* leaves the candidates for good (its remaining decrements keep it negative)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(J.cnt + vstar, INT32_MIN / 2);
-    if (!grid_barrier(J.sync)) return;
+    unsigned int nchunks = 0;
+    if (!grid_barrier(J.sync, chunks, &nchunks)) return;
     // the other parity's queue was drained in the previous pick: reset it for the next one
     if (blockIdx.x == 0 && threadIdx.x == 0) J.sync[SYNC_CHUNKS + ((i + 1) & 1) * 16] = 0u;
-    const unsigned int nchunks = *(volatile unsigned int*)chunks;
     if (nchunks > 0) {
       for (int64_t c = warp; c < (int64_t)nchunks; c += nwarps) {
         const unsigned long long e = J.chunk_q[c];
@@ -441,7 +626,8 @@ cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int*
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int blocks = num_sms;
-  if (blocks > J.partial_cap) return cudaErrorInvalidValue;
+  if (2 * blocks > J.partial_cap) return cudaErrorInvalidValue;
+  if ((long long)blocks * HBINS < CACHE_MAX) return cudaErrorInvalidConfiguration;  // cache slices fit in shared memory
   *blocks_used = blocks;
   GreedyJob j = J;
   void* args[] = {&j};

@@ -150,6 +150,9 @@ struct GreedyJob {
                                 // chunk-queue lengths [96], [112]
   unsigned long long* chunk_q;  // (set, first member) of queued decrement chunks
   int64_t chunk_cap;
+  unsigned int* hist;           // 2 x 4096 gain-histogram bins, zeroed
+  int32_t* cache;               // 2 x 8192 candidate nodes
+  unsigned int* cache_n;        // 2 counts, zeroed
 };
 // All k picks in one cooperative launch (bounded grid barriers).
 cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used);

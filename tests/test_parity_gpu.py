@@ -129,6 +129,33 @@ def test_greedy_k_equals_n():
 
 
 @pytest.mark.parametrize("model", [oracle.IC, oracle.LT])
+def test_greedy_long_k_candidate_cache(model):
+    # thousands of picks on a 2^15-node graph: the greedy kernel rebuilds its
+    # candidate cache many times, misses it, and falls back to full scans
+    el = inputs.rmat(15, 1 << 18, seed=11)
+    og, gg = _pair(el)
+    N = 40_000
+    op, gp = _check_pool(og, gg, model, seed=3, stream=0, N=N)
+    for k in (9, 300, 3000):
+        os_, og_, oc = op.max_coverage(N, k)
+        gs_, gg_, gc = gp.max_coverage(N, k)
+        assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
+
+
+def test_greedy_flat_gains_ties():
+    # an edgeless graph: every RR set is its root alone, gains are small and
+    # heavily tied, so the smallest-id tie rule decides most picks
+    el = inputs.edges(20_000, [])
+    og, gg = _pair(el)
+    N = 30_000
+    op, gp = _check_pool(og, gg, oracle.IC, seed=8, stream=0, N=N)
+    for k in (100, 6000):
+        os_, og_, oc = op.max_coverage(N, k)
+        gs_, gg_, gc = gp.max_coverage(N, k)
+        assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
+
+
+@pytest.mark.parametrize("model", [oracle.IC, oracle.LT])
 def test_estimate_inf(model):
     og, gg = _pair(c1_edges())
     op = oracle.Pool(og, model, 1, 0).grow(3000)
