@@ -503,8 +503,7 @@ struct Cover {
   uint8_t* covered = nullptr;
   int64_t covered_cap = 0;
   uint8_t* in_seed = nullptr;
-  unsigned long long* partial = nullptr;
-  int partial_cap = 0;
+  unsigned long long* argmax = nullptr;  // greedy argmax slots (3, one 128-byte line apart)
   unsigned int* sync = nullptr;
   unsigned long long* chunk_q = nullptr;
   int64_t chunk_cap = 0;
@@ -530,8 +529,7 @@ struct Cover {
     TRY(dev_alloc(&cur, (size_t)n + 1, X.st));
     TRY(dev_alloc(&in_seed, (size_t)n_pad, X.st));
     CU(cudaMallocAsync(&scan_tmp, scan_tmp_bytes(n), X.st));
-    partial_cap = X.num_sms * 8;
-    TRY(dev_alloc(&partial, (size_t)partial_cap, X.st));
+    TRY(dev_alloc(&argmax, 48, X.st));
     TRY(dev_alloc(&sync, 128, X.st));
     TRY(dev_alloc(&hist, 2 * 4096 + 2, X.st));
     TRY(dev_alloc(&cache, 2 * 8192, X.st));
@@ -555,7 +553,7 @@ struct Cover {
     scan_tmp = nullptr;
     dev_free(covered, st);
     dev_free(in_seed, st);
-    dev_free(partial, st);
+    dev_free(argmax, st);
     dev_free(sync, st);
     dev_free(chunk_q, st);
     dev_free(hist, st);
@@ -627,6 +625,8 @@ struct Cover {
 
   // Max-Coverage (Algorithm 2) over sets [0, N): seeds/gains to host.
   ssa_status greedy(const DevPool& P, int64_t N, int k, int32_t* seeds, int64_t* gains, int64_t* cov, Exec& X) {
+    // packed argmax keys (gain + 1) << 32 | ~v stay below 2^63
+    if (N >= INT32_MAX) return fail(SSA_E_ARG, "greedy over %lld sets: at most 2^31 - 2", (long long)N);
     TRY(build_index(P, N, X));
     if (k > k_cap) {
       dev_free(d_seeds, X.st);
@@ -646,6 +646,7 @@ struct Cover {
     CU(cudaMemsetAsync(covered, 0, (size_t)std::max<int64_t>(N, 1), X.st));
     CU(cudaMemsetAsync(sync, 0, sizeof(unsigned int) * 128, X.st));
     CU(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * (2 * 4096 + 2), X.st));
+    CU(cudaMemsetAsync(argmax, 0, sizeof(unsigned long long) * 48, X.st));
     // padding nodes can never be picked
     if (n_pad > n) CU(cudaMemsetAsync(cnt + n, 0xC0, sizeof(int32_t) * (size_t)(n_pad - n), X.st));
     GreedyJob J{};
@@ -661,8 +662,7 @@ struct Cover {
     J.seeds = d_seeds;
     J.gains = d_gains;
     J.k = k;
-    J.partial = partial;
-    J.partial_cap = partial_cap;
+    J.argmax = argmax;
     J.sync = sync;
     J.chunk_q = chunk_q;
     J.chunk_cap = chunk_cap;

@@ -5,10 +5,10 @@
 // (node, sample) entries, exclusive scan into inv_off, scatter of sample ids
 // into inv_samp (order inside a list is irrelevant: each step only needs the
 // set of samples holding the picked node).
-// Greedy step: atomic-free argmax over packed keys (gain+1)<<32 | ~v (largest
-// gain, then smallest id; seeds keyed to 0) as per-block partials, then one
-// kernel that reduces the partials, records the pick and, warp per newly
-// covered set, decrements the gains of the set's members.
+// Greedy: one persistent cooperative kernel for all k picks; a pick is the
+// maximum packed key (gain+1)<<32 | ~v (largest gain, then smallest id; picked
+// nodes keyed to 0), then warps decrement the gains of the members of each
+// newly covered set.
 #include "device.cuh"
 
 namespace ssa {
@@ -147,42 +147,46 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
 constexpr int SYNC_COUNT = 0, SYNC_GEN = 32, SYNC_ERR = 64, SYNC_CHUNKS = 96, SYNC_WORDS = 128;
 constexpr int DEC_CHUNK = 2048;  // covered sets longer than this are decremented in chunks by all warps
 constexpr int CACHE_MAX = 8192;  // greedy candidate cache entries
+constexpr int ARGMAX_STRIDE = 16;  // argmax slots one 128-byte line apart
 constexpr int HBINS = 4096;      // gain histogram: gain g >= 1 counts in bin min(g, HBINS - 1)
 
-// Grid barrier for a cooperative launch.  The generation word and a 32-bit
-// value published by the last block to arrive share one 64-bit word, so a
-// waiter learns both from the poll that releases it: with `publish` given,
-// *info receives *publish as it stood after every block's writes before the
-// barrier.  A wait gives up after ~seconds, sets sync[SYNC_ERR] and returns
-// false; that block then leaves the kernel, and the others give up at their
-// next barrier, since it never arrives.
-__device__ __forceinline__ bool grid_barrier(unsigned int* sync, const unsigned int* publish = nullptr,
-                                             unsigned int* info = nullptr) {
-  __shared__ unsigned int s_info, s_ok;
+// Grid barrier for a cooperative launch.  The release word holds a sense bit
+// (bit 0, flipped by each release) and a 63-bit value published by the last
+// block to arrive, so a waiter learns both from the poll that releases it:
+// *info receives *pub32 or *pub64 (< 2^63) as it stood after every block's
+// writes before the barrier.  A wait gives up after ~seconds, sets
+// sync[SYNC_ERR] and returns false; that block then leaves the kernel, and the
+// others give up at their next barrier, since it never arrives.
+__device__ __forceinline__ bool grid_barrier(unsigned int* sync, const unsigned int* pub32 = nullptr,
+                                             const unsigned long long* pub64 = nullptr,
+                                             unsigned long long* info = nullptr) {
+  __shared__ unsigned long long s_info;
+  __shared__ unsigned int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned long long* gw = reinterpret_cast<volatile unsigned long long*>(sync + SYNC_GEN);
-    const unsigned int g = (unsigned int)*gw;
-    unsigned int got = 0, ok = 1;
+    const unsigned long long sense = *gw & 1ull;
+    unsigned long long got = 0, w = 0;
+    unsigned int ok = 1;
     __threadfence();
     if (atomicAdd(sync + SYNC_COUNT, 1u) + 1u == gridDim.x) {
       atomicExch(sync + SYNC_COUNT, 0u);
       __threadfence();
-      if (publish) got = *(volatile const unsigned int*)publish;
-      atomicExch((unsigned long long*)gw, ((unsigned long long)got << 32) | (unsigned long long)(g + 1u));
+      if (pub32) got = *(volatile const unsigned int*)pub32;
+      if (pub64) got = *(volatile const unsigned long long*)pub64;
+      atomicExch((unsigned long long*)gw, (got << 1) | (sense ^ 1ull));
     } else {
       unsigned int ns = 8;
-      unsigned long long w;
-      for (long long spins = 0; (unsigned int)(w = *gw) == g; ++spins) {
+      for (long long spins = 0; ((w = *gw) & 1ull) == sense; ++spins) {
         if (spins > (1ll << 22)) {  // seconds: a barrier never takes that long
           atomicExch(sync + SYNC_ERR, 1u);
           ok = 0;
           break;
         }
         __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (ns < 128) ns <<= 1;
       }
-      got = (unsigned int)(w >> 32);
+      got = w >> 1;
     }
     __threadfence();
     s_info = got;
@@ -210,11 +214,27 @@ __device__ __forceinline__ void decrement_members(int32_t* cnt, const int32_t* m
   for (; t < len; t += 32) atomicSub(cnt + __ldg(mem + t), 1);
 }
 
+// Grid-wide maximum of the threads' keys (< 2^63): each block folds its own
+// into one of three slots by atomicMax, and the barrier publishes the slot.
+// Argmax number a uses slot a % 3; block 0 clears slot (a + 2) % 3 after the
+// barrier, which no block writes before the next barrier has completed.
+__device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long long& best, unsigned long long* s_red,
+                                            int& n_argmax) {
+  best = block_max(best, s_red);
+  const int slot = n_argmax % 3;
+  n_argmax += 1;
+  unsigned long long* slots = J.argmax;
+  if (threadIdx.x == 0 && best != 0ull) atomicMax(slots + slot * ARGMAX_STRIDE, best);
+  if (!grid_barrier(J.sync, nullptr, slots + slot * ARGMAX_STRIDE, &best)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) slots[((slot + 2) % 3) * ARGMAX_STRIDE] = 0ull;
+  return true;
+}
+
 // Persistent greedy: all k picks of Algorithm 2 in one cooperative launch.
 //
 // Argmax.  A pick needs the node of largest gain, then smallest id (picked
-// nodes hold a negative gain); blocks write per-block maxima of packed keys,
-// meet at a grid barrier and all reduce the same partials.  Gains only fall,
+// nodes hold a negative gain); a grid barrier publishes the maximum of the
+// blocks' packed keys to every block.  Gains only fall,
 // so after a scan of all n nodes that finds the threshold g* with at most
 // CACHE_MAX nodes of gain >= g*, those nodes form a candidate cache: while the
 // best cached gain is still >= g*, it beats every node outside (all <= g* - 1,
@@ -237,9 +257,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   const int64_t warp = gtid >> 5, nwarps = gthreads >> 5;
   const int64_t n4 = J.n_pad >> 2;
   const int4* c4 = reinterpret_cast<const int4*>(J.cnt);
-  // partials: [0, grid) for cache scans, [grid, 2 grid) for full scans, so a
-  // full scan after a missed cache never overwrites partials still being read
-  unsigned long long* part_full = J.partial + gridDim.x;
+  int n_argmax = 0;
   // Rebuild policy (every block tracks the same values): the first pick only
   // scans; a rebuild needs at least REBUILD_MIN picks left; a cache that served
   // fewer than REBUILD_MIN picks, or a rebuild that found no threshold,
@@ -275,16 +293,8 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
           const unsigned long long key = gain_key(__ldcg(J.cnt + v), (uint32_t)v);
           best = key > best ? key : best;
         }
-        best = block_max(best, s_red);
-        if (threadIdx.x == 0) J.partial[blockIdx.x] = best;
-        if (!grid_barrier(J.sync)) return;
-        best = 0;
-        for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
-          const unsigned long long key = __ldcg(J.partial + t);
-          best = key > best ? key : best;
-        }
-        best = block_max(best, s_red);
-        // every block reduced the same partials, so all take the same branch
+        if (!grid_argmax(J, best, s_red, n_argmax)) return;
+        // every block holds the same maximum, so all take the same branch
         have = best != 0 && (int)((uint32_t)(best >> 32) - 1u) >= gstar;
       }
       if (!have) {
@@ -324,20 +334,12 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
           if (c.w >= floor_g) atomicAdd(s_hist + min(c.w - floor_g, HBINS - 1), 1u);
         }
       }
-      best = block_max(best, s_red);
-      if (threadIdx.x == 0) part_full[blockIdx.x] = best;
       if (rebuild) {
         unsigned int* h = J.hist + (size_t)hb * HBINS;
         for (int t = threadIdx.x; t < HBINS; t += blockDim.x)
           if (s_hist[t]) atomicAdd(h + t, s_hist[t]);
       }
-      if (!grid_barrier(J.sync)) return;
-      best = 0;
-      for (int t = threadIdx.x; t < (int)gridDim.x; t += blockDim.x) {
-        const unsigned long long key = __ldcg(part_full + t);
-        best = key > best ? key : best;
-      }
-      best = block_max(best, s_red);
+      if (!grid_argmax(J, best, s_red, n_argmax)) return;
       if (rebuild) {
         // g* = floor + the smallest bin b with at most CACHE_MAX nodes in
         // bins >= b: a descending block scan of the merged histogram (thread t
@@ -448,8 +450,8 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
     }
     // v* leaves the candidates for good (its remaining decrements keep it negative)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(J.cnt + vstar, INT32_MIN / 2);
-    unsigned int nchunks = 0;
-    if (!grid_barrier(J.sync, chunks, &nchunks)) return;
+    unsigned long long nchunks = 0;
+    if (!grid_barrier(J.sync, chunks, nullptr, &nchunks)) return;
     // the other parity's queue was drained in the previous pick: reset it for the next one
     if (blockIdx.x == 0 && threadIdx.x == 0) J.sync[SYNC_CHUNKS + ((i + 1) & 1) * 16] = 0u;
     if (nchunks > 0) {
@@ -626,7 +628,6 @@ cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int*
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int blocks = num_sms;
-  if (2 * blocks > J.partial_cap) return cudaErrorInvalidValue;
   if ((long long)blocks * HBINS < CACHE_MAX) return cudaErrorInvalidConfiguration;  // cache slices fit in shared memory
   *blocks_used = blocks;
   GreedyJob j = J;

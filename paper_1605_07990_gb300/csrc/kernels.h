@@ -144,10 +144,9 @@ struct GreedyJob {
   int32_t* seeds;               // k (device)
   int32_t* gains;               // k (device)
   int k;
-  unsigned long long* partial;  // one per block
-  int partial_cap;
-  unsigned int* sync;           // 128 words, zeroed: count [0], generation [32], timeout flag [64],
-                                // chunk-queue lengths [96], [112]
+  unsigned long long* argmax;   // 3 argmax slots 16 words apart, zeroed
+  unsigned int* sync;           // 128 words, zeroed: count [0], release word (64-bit) [32],
+                                // timeout flag [64], chunk-queue lengths [96], [112]
   unsigned long long* chunk_q;  // (set, first member) of queued decrement chunks
   int64_t chunk_cap;
   unsigned int* hist;           // 2 x 4096 gain-histogram bins, zeroed
