@@ -625,7 +625,7 @@ struct Cover {
 
   // Max-Coverage (Algorithm 2) over sets [0, N): seeds/gains to host.
   ssa_status greedy(const DevPool& P, int64_t N, int k, int32_t* seeds, int64_t* gains, int64_t* cov, Exec& X) {
-    // packed argmax keys (gain + 1) << 32 | ~v stay below 2^63
+    // packed argmax keys (gain + 1) << 31 | (2^31 - 1 - v) stay below 2^62
     if (N >= INT32_MAX) return fail(SSA_E_ARG, "greedy over %lld sets: at most 2^31 - 2", (long long)N);
     TRY(build_index(P, N, X));
     if (k > k_cap) {

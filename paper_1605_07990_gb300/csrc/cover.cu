@@ -142,64 +142,76 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
   return x;
 }
 
-// sync layout: arrival count, generation and timeout flag on separate
+// sync layout: arrival count, release word and timeout flag on separate
 // 128-byte lines so that polling does not contend with the arrivals.
 constexpr int SYNC_COUNT = 0, SYNC_GEN = 32, SYNC_ERR = 64, SYNC_CHUNKS = 96, SYNC_WORDS = 128;
-constexpr int DEC_CHUNK = 2048;  // covered sets longer than this are decremented in chunks by all warps
-constexpr int CACHE_MAX = 8192;  // greedy candidate cache entries
+constexpr int DEC_CHUNK = 2048;    // covered sets longer than this are decremented in chunks by all warps
+constexpr int CACHE_MAX = 8192;    // greedy candidate cache entries
 constexpr int ARGMAX_STRIDE = 16;  // argmax slots one 128-byte line apart
-constexpr int HBINS = 4096;      // gain histogram: gain g >= 1 counts in bin min(g, HBINS - 1)
+constexpr int HBINS = 4096;        // gain histogram: gain g >= floor counts in bin min(g - floor, HBINS - 1)
+constexpr unsigned long long PENDING = 1ull << 62;  // barrier payload flag: decrement chunks are queued
 
-// Grid barrier for a cooperative launch.  The release word holds a sense bit
-// (bit 0, flipped by each release) and a 63-bit value published by the last
-// block to arrive, so a waiter learns both from the poll that releases it:
-// *info receives *pub32 or *pub64 (< 2^63) as it stood after every block's
-// writes before the barrier.  A wait gives up after ~seconds, sets
-// sync[SYNC_ERR] and returns false; that block then leaves the kernel, and the
-// others give up at their next barrier, since it never arrives.
-__device__ __forceinline__ bool grid_barrier(unsigned int* sync, const unsigned int* pub32 = nullptr,
-                                             const unsigned long long* pub64 = nullptr,
-                                             unsigned long long* info = nullptr) {
+// Grid barrier for a cooperative launch.  The last block to arrive runs f()
+// (all its threads; f sees every block's writes from before the barrier) and
+// publishes the result (< 2^63) in the release word beside a sense bit (bit 0,
+// flipped by each release), so every waiter learns it from the poll that
+// releases it; all threads get it in `info`.  A wait gives up after about a
+// second, sets sync[SYNC_ERR] and returns false; that block then leaves the
+// kernel, and the others give up at their next barrier, which it never reaches.
+template <class F>
+__device__ __forceinline__ bool grid_barrier(unsigned int* sync, F&& f, unsigned long long& info) {
   __shared__ unsigned long long s_info;
-  __shared__ unsigned int s_ok;
+  __shared__ unsigned int s_last, s_ok, s_sense;
+  volatile unsigned long long* gw = reinterpret_cast<volatile unsigned long long*>(sync + SYNC_GEN);
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned long long* gw = reinterpret_cast<volatile unsigned long long*>(sync + SYNC_GEN);
-    const unsigned long long sense = *gw & 1ull;
-    unsigned long long got = 0, w = 0;
-    unsigned int ok = 1;
+    s_sense = (unsigned int)(*gw & 1ull);
+    s_ok = 1;
     __threadfence();
-    if (atomicAdd(sync + SYNC_COUNT, 1u) + 1u == gridDim.x) {
+    const bool last = atomicAdd(sync + SYNC_COUNT, 1u) + 1u == gridDim.x;
+    if (last) {
       atomicExch(sync + SYNC_COUNT, 0u);
       __threadfence();
-      if (pub32) got = *(volatile const unsigned int*)pub32;
-      if (pub64) got = *(volatile const unsigned long long*)pub64;
-      atomicExch((unsigned long long*)gw, (got << 1) | (sense ^ 1ull));
-    } else {
-      unsigned int ns = 8;
-      for (long long spins = 0; ((w = *gw) & 1ull) == sense; ++spins) {
-        if (spins > (1ll << 22)) {  // seconds: a barrier never takes that long
-          atomicExch(sync + SYNC_ERR, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(ns);
-        if (ns < 128) ns <<= 1;
-      }
-      got = w >> 1;
     }
-    __threadfence();
-    s_info = got;
-    s_ok = ok;
+    s_last = last;
   }
   __syncthreads();
-  if (info) *info = s_info;
+  if (s_last) {
+    const unsigned long long r = f();
+    if (threadIdx.x == 0) {
+      atomicExch((unsigned long long*)gw, (r << 1) | (unsigned long long)(s_sense ^ 1u));
+      s_info = r;
+    }
+  } else if (threadIdx.x == 0) {
+    unsigned long long w;
+    unsigned int ns = 8;
+    for (long long spins = 0; (unsigned int)((w = *gw) & 1ull) == s_sense; ++spins) {
+      if (spins > (1ll << 22)) {  // seconds: a barrier never takes that long
+        atomicExch(sync + SYNC_ERR, 1u);
+        s_ok = 0;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 128) ns <<= 1;
+    }
+    s_info = w >> 1;
+    __threadfence();
+  }
+  __syncthreads();
+  info = s_info;
   return s_ok != 0u;
 }
 
+// Packed argmax key: larger gain first, then smaller id; picked nodes (negative
+// gain) key to 0.  With gains below 2^31 - 1 and ids below 2^31, keys stay
+// below 2^62, under the barrier payload's PENDING flag.
 __device__ __forceinline__ unsigned long long gain_key(int32_t c, uint32_t v) {
-  return c < 0 ? 0ull : (((unsigned long long)(uint32_t)(c + 1)) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
+  return c < 0 ? 0ull : (((unsigned long long)(uint32_t)(c + 1)) << 31) | (unsigned long long)(0x7FFFFFFFu - v);
 }
+__device__ __forceinline__ int32_t key_node(unsigned long long key) {
+  return (int32_t)(0x7FFFFFFFu - (uint32_t)(key & 0x7FFFFFFFull));
+}
+__device__ __forceinline__ int32_t key_gain(unsigned long long key) { return (int32_t)(key >> 31) - 1; }
 
 // gains of the `len` members at mem lose one each (a warp, lanes striped)
 __device__ __forceinline__ void decrement_members(int32_t* cnt, const int32_t* mem, int32_t len, int lane) {
@@ -214,33 +226,34 @@ __device__ __forceinline__ void decrement_members(int32_t* cnt, const int32_t* m
   for (; t < len; t += 32) atomicSub(cnt + __ldg(mem + t), 1);
 }
 
-// Grid-wide maximum of the threads' keys (< 2^63): each block folds its own
-// into one of three slots by atomicMax, and the barrier publishes the slot.
-// Argmax number a uses slot a % 3; block 0 clears slot (a + 2) % 3 after the
-// barrier, which no block writes before the next barrier has completed.
+// Grid-wide maximum of the threads' keys, in every thread: each block folds
+// its own into one of three slots by atomicMax, and the barrier publishes the
+// slot.  Argmax number a uses slot a % 3; block 0 clears slot (a + 2) % 3 after
+// the barrier, which no block writes before the next barrier has completed.
 __device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long long& best, unsigned long long* s_red,
                                             int& n_argmax) {
   best = block_max(best, s_red);
   const int slot = n_argmax % 3;
   n_argmax += 1;
-  unsigned long long* slots = J.argmax;
-  if (threadIdx.x == 0 && best != 0ull) atomicMax(slots + slot * ARGMAX_STRIDE, best);
-  if (!grid_barrier(J.sync, nullptr, slots + slot * ARGMAX_STRIDE, &best)) return false;
-  if (blockIdx.x == 0 && threadIdx.x == 0) slots[((slot + 2) % 3) * ARGMAX_STRIDE] = 0ull;
+  unsigned long long* at = J.argmax + slot * ARGMAX_STRIDE;
+  if (threadIdx.x == 0 && best != 0ull) atomicMax(at, best);
+  if (!grid_barrier(J.sync, [&] { return __ldcg(at); }, best)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) J.argmax[((slot + 2) % 3) * ARGMAX_STRIDE] = 0ull;
   return true;
 }
 
 // Persistent greedy: all k picks of Algorithm 2 in one cooperative launch.
 //
-// Argmax.  A pick needs the node of largest gain, then smallest id (picked
-// nodes hold a negative gain); a grid barrier publishes the maximum of the
-// blocks' packed keys to every block.  Gains only fall,
-// so after a scan of all n nodes that finds the threshold g* with at most
-// CACHE_MAX nodes of gain >= g*, those nodes form a candidate cache: while the
-// best cached gain is still >= g*, it beats every node outside (all <= g* - 1,
-// ties included), and the pick scans the cache instead of all n nodes.  When
-// the best cached gain falls below g*, the pick scans all n nodes and builds
-// a new cache from a gain histogram taken in the same pass.
+// Argmax.  A pick needs the node of largest gain, then smallest id.  Gains only
+// fall, so after a scan of all n nodes that finds the threshold g* with at
+// most CACHE_MAX nodes of gain >= g*, those nodes form a candidate cache: while
+// the best cached gain is still >= g*, it beats every node outside (all
+// <= g* - 1, ties included).  Every block holds the whole cache in shared
+// memory, and the last block to reach the barrier that ends a pick computes
+// the next pick's argmax over it, published with the release: a cached pick
+// costs one grid barrier.  When the best cached gain falls below g*, the pick
+// scans all n nodes (a second barrier publishes the maximum of the blocks'
+// keys) and builds a new cache from a gain histogram taken in the same pass.
 //
 // Cover.  Warps walk v*'s inverted lists of all index batches and, for each
 // newly covered set, decrement the gains of its members; sets longer than
@@ -249,8 +262,12 @@ __device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long lo
 __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   __shared__ unsigned long long s_red[32];
   __shared__ int64_t s_lo[GREEDY_MAX_LISTS], s_hi[GREEDY_MAX_LISTS];
-  __shared__ unsigned int s_hist[HBINS];
+  // the gain histogram (HBINS) and the staged cache (CACHE_MAX ids) share
+  // space: a histogram is only taken after the cache has been dropped
+  __shared__ unsigned int s_buf[CACHE_MAX > HBINS ? CACHE_MAX : HBINS];
   __shared__ long long s_scan[32], s_scan_tot;
+  unsigned int* s_hist = s_buf;
+  int32_t* s_cache = reinterpret_cast<int32_t*>(s_buf);
   const int lane = threadIdx.x & 31;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -264,39 +281,49 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   // postpones the next rebuild by a doubling back-off.
   constexpr int REBUILD_MIN = 8;
   int rebuilds = 0, next_try = 1, backoff = REBUILD_MIN, built_at = 0, gstar = 0, g_prev = 0;
-  bool cached = false, stage = false;
-  int my_nc = 0;
-  // a block's cache slice, at most ceil(CACHE_MAX / grid) <= HBINS entries,
-  // shares the histogram's space: a histogram is only taken after a cache miss
-  int32_t* s_cand = reinterpret_cast<int32_t*>(s_hist);
+  bool cached = false, stage = false, fused_ok = false;
+  int nc = 0;                          // staged cache entries
+  unsigned long long fused_key = 0;    // this pick's argmax, from the previous pick's last barrier
+  // block-wide argmax over the staged cache, for the last block at a barrier
+  auto cache_argmax = [&]() -> unsigned long long {
+    unsigned long long b = 0;
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      const int32_t v = s_cache[t];
+      const unsigned long long key = gain_key(__ldcg(J.cnt + v), (uint32_t)v);
+      b = key > b ? key : b;
+    }
+    return block_max(b, s_red);
+  };
   for (int i = 0; i < J.k; ++i) {
     unsigned long long best = 0;
     bool have = false;
     if (cached) {
+      bool valid = false;
       if (stage) {
-        // first pick on a new cache: this block's slice (entries blockIdx.x +
-        // s * grid) moves to shared memory, so later picks gather only gains
+        // first pick on a new cache: every block stages all of it, and the
+        // blocks scan interleaved slices of it for this pick's argmax
         const int cb = (rebuilds - 1) & 1;
-        const unsigned int nc = __ldcg(J.cache_n + cb);
-        my_nc = -1;
-        if (nc <= (unsigned int)CACHE_MAX) {
-          const int32_t* cache = J.cache + (size_t)cb * CACHE_MAX;
-          my_nc = nc > blockIdx.x ? (int)((nc - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
-          for (int t = threadIdx.x; t < my_nc; t += blockDim.x) s_cand[t] = __ldcg(cache + blockIdx.x + (size_t)t * gridDim.x);
-        }
+        const unsigned int m = __ldcg(J.cache_n + cb);
+        nc = m <= (unsigned int)CACHE_MAX ? (int)m : 0;
+        const int32_t* cache = J.cache + (size_t)cb * CACHE_MAX;
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) s_cache[t] = __ldcg(cache + t);
         __syncthreads();
         stage = false;
-      }
-      if (my_nc >= 0) {
-        for (int t = threadIdx.x; t < my_nc; t += blockDim.x) {
-          const int32_t v = s_cand[t];
-          const unsigned long long key = gain_key(__ldcg(J.cnt + v), (uint32_t)v);
-          best = key > best ? key : best;
+        if (m <= (unsigned int)CACHE_MAX) {
+          for (int t = blockIdx.x + (int)threadIdx.x * (int)gridDim.x; t < nc; t += (int)(blockDim.x * gridDim.x)) {
+            const int32_t v = s_cache[t];
+            const unsigned long long key = gain_key(__ldcg(J.cnt + v), (uint32_t)v);
+            best = key > best ? key : best;
+          }
+          if (!grid_argmax(J, best, s_red, n_argmax)) return;
+          valid = true;
         }
-        if (!grid_argmax(J, best, s_red, n_argmax)) return;
-        // every block holds the same maximum, so all take the same branch
-        have = best != 0 && (int)((uint32_t)(best >> 32) - 1u) >= gstar;
+      } else if (fused_ok) {
+        best = fused_key;
+        valid = true;
       }
+      // every block holds the same maximum, so all take the same branch
+      have = valid && best != 0 && key_gain(best) >= gstar;
       if (!have) {
         cached = false;
         if (i - built_at < REBUILD_MIN) {
@@ -336,6 +363,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
       }
       if (rebuild) {
         unsigned int* h = J.hist + (size_t)hb * HBINS;
+        __syncthreads();
         for (int t = threadIdx.x; t < HBINS; t += blockDim.x)
           if (s_hist[t]) atomicAdd(h + t, s_hist[t]);
       }
@@ -365,13 +393,13 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         key = block_max(key, s_red);
         int g = key ? floor_g + (HBINS - (int)key) : 0;
         // a threshold above the best gain would leave the best node outside
-        if (g > (int)((uint32_t)(best >> 32) - 1u)) g = 0;
+        if (g > key_gain(best)) g = 0;
         if (g > 0) {
           // Some blocks may already be covering for this pick, so a gain read
           // here may have fallen since the scan: below g* it stays below for
           // good; at or above g* it was counted in the histogram, which bounds
           // the cache at CACHE_MAX entries.
-          const int32_t vstar = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
+          const int32_t vstar = key_node(best);
           unsigned int* nout = J.cache_n + hb;
           int32_t* out = J.cache + (size_t)hb * CACHE_MAX;
           // warp-uniform trip count, so the ballots below see all 32 lanes
@@ -403,7 +431,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         }
         // this parity's histogram and cache stay read-only until the next
         // rebuild, which uses the other parity: clear that one now (nobody
-        // reads it any more: the last cache scan of it ended at the barrier above)
+        // reads it any more: its last staging ended before the barrier above)
         if (blockIdx.x == 0) {
           for (int t = threadIdx.x; t < HBINS; t += blockDim.x) J.hist[(size_t)(hb ^ 1) * HBINS + t] = 0u;
           if (threadIdx.x == 0) J.cache_n[hb ^ 1] = 0u;
@@ -411,15 +439,15 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         rebuilds += 1;
       }
     }
-    const int32_t vstar = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
-    g_prev = (int)((uint32_t)(best >> 32) - 1u);
+    const int32_t vstar = key_node(best);
+    g_prev = key_gain(best);
     if (threadIdx.x < J.nlists) {
       s_lo[threadIdx.x] = J.lists[threadIdx.x].off[vstar];
       s_hi[threadIdx.x] = J.lists[threadIdx.x].off[vstar + 1];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       J.seeds[i] = vstar;
-      J.gains[i] = (int32_t)((uint32_t)(best >> 32) - 1u);
+      J.gains[i] = key_gain(best);
     }
     __syncthreads();
     unsigned int* chunks = J.sync + SYNC_CHUNKS + (i & 1) * 16;
@@ -450,20 +478,31 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
     }
     // v* leaves the candidates for good (its remaining decrements keep it negative)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(J.cnt + vstar, INT32_MIN / 2);
-    unsigned long long nchunks = 0;
-    if (!grid_barrier(J.sync, chunks, nullptr, &nchunks)) return;
+    // The barrier that ends the pick also yields the next pick's argmax when
+    // the next pick uses a staged cache; queued chunks come first, and then
+    // the drain's barrier yields it instead.
+    const bool fuse = cached && !stage;
+    unsigned long long pay = 0;
+    if (!grid_barrier(J.sync, [&]() -> unsigned long long {
+          const unsigned int m = __ldcg(chunks);
+          if (m > 0u) return PENDING | m;
+          return fuse ? cache_argmax() : 0ull;
+        }, pay)) return;
     // the other parity's queue was drained in the previous pick: reset it for the next one
     if (blockIdx.x == 0 && threadIdx.x == 0) J.sync[SYNC_CHUNKS + ((i + 1) & 1) * 16] = 0u;
-    if (nchunks > 0) {
-      for (int64_t c = warp; c < (int64_t)nchunks; c += nwarps) {
+    if (pay & PENDING) {
+      const int64_t nchunks = (int64_t)(pay & (PENDING - 1ull));
+      for (int64_t c = warp; c < nchunks; c += nwarps) {
         const unsigned long long e = J.chunk_q[c];
         const int32_t j = (int32_t)(e >> 32), from = (int32_t)(uint32_t)e;
         const int32_t len = J.set_len[j];
         const int32_t cnt = min(DEC_CHUNK, len - from);
         decrement_members(J.cnt, J.pool_nodes + J.set_start[j] + from, cnt, lane);
       }
-      if (!grid_barrier(J.sync)) return;
+      if (!grid_barrier(J.sync, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
     }
+    fused_key = pay;
+    fused_ok = fuse;
   }
 }
 
