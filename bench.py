@@ -266,6 +266,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sample-only", type=int, default=0,
                     help="profiling case: only sample this many RR sets of the workload into a pool")
+    ap.add_argument("--then-greedy", type=int, default=0,
+                    help="with --sample-only: also index the pool and run greedy Max-Coverage for this k")
     ap.add_argument("--serving", action="store_true", help="the Poisson serving mix instead of the solve bench")
     ap.add_argument("--queries", type=int, default=2000)
     ap.add_argument("--slots", type=int, default=4)
@@ -295,7 +297,11 @@ def main():
     if args.sample_only:
         pool = P.Pool(g, model, seed=1, stream=0).grow(args.sample_only)
         torch.cuda.synchronize()
-        print(json.dumps({"sample_only": args.sample_only, "pool": pool.info()}))
+        out = {"sample_only": args.sample_only, "pool": pool.info()}
+        if args.then_greedy:
+            _, gains, cov = pool.max_coverage(args.sample_only, args.then_greedy)
+            out["greedy"] = {"k": args.then_greedy, "cov": int(cov)}
+        print(json.dumps(out))
         pool.free()
         g.free()
         return 0

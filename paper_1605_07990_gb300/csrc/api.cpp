@@ -529,7 +529,7 @@ struct Cover {
     TRY(dev_alloc(&cur, (size_t)n + 1, X.st));
     TRY(dev_alloc(&in_seed, (size_t)n_pad, X.st));
     CU(cudaMallocAsync(&scan_tmp, scan_tmp_bytes(n), X.st));
-    TRY(dev_alloc(&argmax, 48, X.st));
+    TRY(dev_alloc(&argmax, 64 + 2 * 1024, X.st));
     TRY(dev_alloc(&sync, 128, X.st));
     TRY(dev_alloc(&hist, 2 * 4096 + 2, X.st));
     TRY(dev_alloc(&cache, 2 * 8192, X.st));
@@ -636,17 +636,20 @@ struct Cover {
       k_cap = k;
     }
     TRY(dev_grow(&covered, &covered_cap, std::max<int64_t>(N, 1), 0, X.st));
+    int64_t total_e = 0;  // entries of sets [0, N), an upper bound when N cuts a batch
     {
-      // queued decrement chunks of one pick: at most one per 2048 entries of [0, N)
+      // queued decrement chunks of one pick: a set longer than 2048 entries
+      // queues ceil(len / 2048) < len / 1024 chunks
       int64_t e0 = 0, e1 = 0;
       P.entry_range(0, N, &e0, &e1);
-      TRY(dev_grow(&chunk_q, &chunk_cap, e1 / 2048 + 1, 0, X.st));
+      total_e = e1 - e0;
+      TRY(dev_grow(&chunk_q, &chunk_cap, e1 / 1024 + 1, 0, X.st));
     }
     int h = X.begin(SSA_K_GREEDY);
     CU(cudaMemsetAsync(covered, 0, (size_t)std::max<int64_t>(N, 1), X.st));
     CU(cudaMemsetAsync(sync, 0, sizeof(unsigned int) * 128, X.st));
     CU(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * (2 * 4096 + 2), X.st));
-    CU(cudaMemsetAsync(argmax, 0, sizeof(unsigned long long) * 48, X.st));
+    CU(cudaMemsetAsync(argmax, 0, sizeof(unsigned long long) * (64 + 2 * 1024), X.st));
     // padding nodes can never be picked
     if (n_pad > n) CU(cudaMemsetAsync(cnt + n, 0xC0, sizeof(int32_t) * (size_t)(n_pad - n), X.st));
     GreedyJob J{};
@@ -663,6 +666,8 @@ struct Cover {
     J.gains = d_gains;
     J.k = k;
     J.argmax = argmax;
+    J.n_sets = N;
+    J.total_entries = (unsigned long long)total_e;
     J.sync = sync;
     J.chunk_q = chunk_q;
     J.chunk_cap = chunk_cap;
@@ -683,6 +688,7 @@ struct Cover {
     CU(cudaMemcpyAsync(g32.data(), d_gains, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
     CU(cudaMemcpyAsync(hsync, sync, sizeof(hsync), cudaMemcpyDeviceToHost, X.st));
     CU(cudaStreamSynchronize(X.st));
+    if (hsync[64] == 2u) return fail(SSA_E_INTERNAL, "greedy decrement queue overflow");
     if (hsync[64]) return fail(SSA_E_TIMEOUT, "greedy grid barrier timed out");
     int64_t c = 0;
     for (int i = 0; i < k; ++i) {

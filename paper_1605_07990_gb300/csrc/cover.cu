@@ -118,12 +118,14 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int32_t* in, int64_t n
 
 // ---- greedy ----
 
-__device__ __forceinline__ unsigned long long block_max(unsigned long long x, unsigned long long* s) {
+// maximum (or sum) over the block of x, in every thread
+template <bool SUM>
+__device__ __forceinline__ unsigned long long block_reduce(unsigned long long x, unsigned long long* s) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int d = 16; d; d >>= 1) {
     const unsigned long long t = __shfl_xor_sync(FULL_MASK, x, d);
-    x = t > x ? t : x;
+    x = SUM ? x + t : (t > x ? t : x);
   }
   if (lane == 0) s[wid] = x;
   __syncthreads();
@@ -132,7 +134,7 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
 #pragma unroll
     for (int d = 16; d; d >>= 1) {
       const unsigned long long t = __shfl_xor_sync(FULL_MASK, x, d);
-      x = t > x ? t : x;
+      x = SUM ? x + t : (t > x ? t : x);
     }
     if (lane == 0) s[0] = x;
   }
@@ -140,6 +142,9 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
   x = s[0];
   __syncthreads();
   return x;
+}
+__device__ __forceinline__ unsigned long long block_max(unsigned long long x, unsigned long long* s) {
+  return block_reduce<false>(x, s);
 }
 
 // sync layout: arrival count, release word and timeout flag on separate
@@ -150,6 +155,11 @@ constexpr int CACHE_MAX = 8192;    // greedy candidate cache entries
 constexpr int ARGMAX_STRIDE = 16;  // argmax slots one 128-byte line apart
 constexpr int HBINS = 4096;        // gain histogram: gain g >= floor counts in bin min(g - floor, HBINS - 1)
 constexpr unsigned long long PENDING = 1ull << 62;  // barrier payload flag: decrement chunks are queued
+constexpr unsigned long long RECOUNT = 1ull << 61;  // with PENDING: recount the gains instead of draining
+// per-block entry tallies (64-bit slots after the argmax slots): entries of
+// all sets the block covered so far, and entries it queued in the last pick
+// that queued any
+constexpr int ACC_DONE = 64, ACC_QUEUED = 64 + 1024;
 
 // Grid barrier for a cooperative launch.  The last block to arrive runs f()
 // (all its threads; f sees every block's writes from before the barrier) and
@@ -256,9 +266,14 @@ __device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long lo
 // keys) and builds a new cache from a gain histogram taken in the same pass.
 //
 // Cover.  Warps walk v*'s inverted lists of all index batches and, for each
-// newly covered set, decrement the gains of its members; sets longer than
-// DEC_CHUNK are split into chunks queued for every warp after the barrier
-// that closes the pick.  Barrier waits are bounded (sync[SYNC_ERR] on timeout).
+// newly covered set, decrement the gains of its members.  Sets longer than
+// DEC_CHUNK go whole, as chunks, to a queue that every warp drains after the
+// barrier that closes the pick.  When the queued entries outnumber the
+// entries of the sets still uncovered (one pick can cover a bulk of huge sets
+// that share one core of nodes), the last block at that barrier calls for a
+// recount instead: gains are rebuilt from the uncovered sets, which costs
+// fewer atomics than the decrements would.  Barrier waits are bounded
+// (sync[SYNC_ERR] on timeout).
 __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   __shared__ unsigned long long s_red[32];
   __shared__ int64_t s_lo[GREEDY_MAX_LISTS], s_hi[GREEDY_MAX_LISTS];
@@ -266,6 +281,8 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   // space: a histogram is only taken after the cache has been dropped
   __shared__ unsigned int s_buf[CACHE_MAX > HBINS ? CACHE_MAX : HBINS];
   __shared__ long long s_scan[32], s_scan_tot;
+  __shared__ unsigned long long s_cov_e, s_queued_e;  // entries of the sets this block covered / queued
+  unsigned long long my_done = 0, my_queued = 0;      // thread 0: this block's slot values
   unsigned int* s_hist = s_buf;
   int32_t* s_cache = reinterpret_cast<int32_t*>(s_buf);
   const int lane = threadIdx.x & 31;
@@ -449,6 +466,10 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
       J.seeds[i] = vstar;
       J.gains[i] = key_gain(best);
     }
+    if (threadIdx.x == 0) {
+      s_cov_e = 0ull;
+      s_queued_e = 0ull;
+    }
     __syncthreads();
     unsigned int* chunks = J.sync + SYNC_CHUNKS + (i & 1) * 16;
     for (int b = 0; b < J.nlists; ++b) {
@@ -462,18 +483,25 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         if (was) continue;
         __syncwarp();
         if (lane == 0) J.covered[j] = 1;
-        int32_t mine = len;
+        if (lane == 0) atomicAdd(&s_cov_e, (unsigned long long)len);
         if (len > DEC_CHUNK) {
-          // keep the first chunk, queue the rest for every warp after the barrier
-          mine = DEC_CHUNK;
-          const int nq = (len - 1) / DEC_CHUNK;
+          // the whole set goes to the queue, for a drain or a recount after the barrier
+          const int nq = (len + DEC_CHUNK - 1) / DEC_CHUNK;
           unsigned int at = 0;
-          if (lane == 0) at = atomicAdd(chunks, (unsigned int)nq);
+          if (lane == 0) {
+            at = atomicAdd(chunks, (unsigned int)nq);
+            atomicAdd(&s_queued_e, (unsigned long long)len);
+          }
           at = __shfl_sync(FULL_MASK, at, 0);
+          if ((int64_t)at + nq > J.chunk_cap) {  // cannot happen with the host's sizing
+            if (lane == 0) atomicExch(J.sync + SYNC_ERR, 2u);
+            continue;
+          }
           for (int c = lane; c < nq; c += 32)
-            J.chunk_q[at + c] = ((unsigned long long)(uint32_t)j << 32) | (uint32_t)((c + 1) * DEC_CHUNK);
+            J.chunk_q[at + c] = ((unsigned long long)(uint32_t)j << 32) | (uint32_t)(c * DEC_CHUNK);
+          continue;
         }
-        decrement_members(J.cnt, J.pool_nodes + start, mine, lane);
+        decrement_members(J.cnt, J.pool_nodes + start, len, lane);
       }
     }
     // v* leaves the candidates for good (its remaining decrements keep it negative)
@@ -483,15 +511,62 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
     // the drain's barrier yields it instead.
     const bool fuse = cached && !stage;
     unsigned long long pay = 0;
+    __syncthreads();
+    // plain stores to the block's own slots, only when they change
+    if (threadIdx.x == 0) {
+      if (s_cov_e) {
+        my_done += s_cov_e;
+        J.argmax[ACC_DONE + blockIdx.x] = my_done;
+      }
+      if (s_queued_e != my_queued) {
+        my_queued = s_queued_e;
+        J.argmax[ACC_QUEUED + blockIdx.x] = my_queued;
+      }
+    }
     if (!grid_barrier(J.sync, [&]() -> unsigned long long {
           const unsigned int m = __ldcg(chunks);
-          if (m > 0u) return PENDING | m;
+          if (m > 0u) {
+            // entries still in uncovered sets after this pick, against the queued ones
+            unsigned long long done = 0, q = 0;
+            if (threadIdx.x < gridDim.x) {
+              done = __ldcg(J.argmax + ACC_DONE + threadIdx.x);
+              q = __ldcg(J.argmax + ACC_QUEUED + threadIdx.x);
+            }
+            done = block_reduce<true>(done, s_red);
+            q = block_reduce<true>(q, s_red);
+            // a recount costs an increment per entry left, a pass over the sets'
+            // flags and the gains, and two more barriers: it must win clearly
+            const unsigned long long left = done < J.total_entries ? J.total_entries - done : 0ull;
+            const unsigned long long fixed = (unsigned long long)(J.n_sets + J.n_pad) / 8 + (1ull << 20);
+            return PENDING | (q > 2 * left + fixed ? RECOUNT : 0ull) | m;
+          }
           return fuse ? cache_argmax() : 0ull;
         }, pay)) return;
     // the other parity's queue was drained in the previous pick: reset it for the next one
     if (blockIdx.x == 0 && threadIdx.x == 0) J.sync[SYNC_CHUNKS + ((i + 1) & 1) * 16] = 0u;
-    if (pay & PENDING) {
-      const int64_t nchunks = (int64_t)(pay & (PENDING - 1ull));
+    if ((pay & PENDING) && (pay & RECOUNT)) {
+      // gains from scratch: zero every unpicked node (picked and padding
+      // nodes stay negative), then one increment per member of each set still
+      // uncovered; no uncovered set holds a picked node
+      for (int64_t q = gtid; q < n4; q += gthreads) {
+        int4 c = __ldcg(c4 + q);
+        c.x = c.x < 0 ? c.x : 0;
+        c.y = c.y < 0 ? c.y : 0;
+        c.z = c.z < 0 ? c.z : 0;
+        c.w = c.w < 0 ? c.w : 0;
+        reinterpret_cast<int4*>(J.cnt)[q] = c;
+      }
+      unsigned long long unused = 0;
+      if (!grid_barrier(J.sync, [] { return 0ull; }, unused)) return;
+      for (int64_t j = warp; j < J.n_sets; j += nwarps) {
+        if (__ldcg(J.covered + j)) continue;
+        const int32_t* mem = J.pool_nodes + J.set_start[j];
+        const int32_t len = J.set_len[j];
+        for (int t = lane; t < len; t += 32) atomicAdd(J.cnt + __ldg(mem + t), 1);
+      }
+      if (!grid_barrier(J.sync, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
+    } else if (pay & PENDING) {
+      const int64_t nchunks = (int64_t)(pay & (RECOUNT - 1ull));
       for (int64_t c = warp; c < nchunks; c += nwarps) {
         const unsigned long long e = J.chunk_q[c];
         const int32_t j = (int32_t)(e >> 32), from = (int32_t)(uint32_t)e;
@@ -667,7 +742,8 @@ cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int*
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int blocks = num_sms;
-  if ((long long)blocks * HBINS < CACHE_MAX) return cudaErrorInvalidConfiguration;  // cache slices fit in shared memory
+  // cache slices fit in shared memory; one tally slot and one reducing thread per block
+  if ((long long)blocks * HBINS < CACHE_MAX || blocks > 1024) return cudaErrorInvalidConfiguration;
   *blocks_used = blocks;
   GreedyJob j = J;
   void* args[] = {&j};

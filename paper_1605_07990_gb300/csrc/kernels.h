@@ -144,7 +144,11 @@ struct GreedyJob {
   int32_t* seeds;               // k (device)
   int32_t* gains;               // k (device)
   int k;
-  unsigned long long* argmax;   // 3 argmax slots 16 words apart, zeroed
+  unsigned long long* argmax;   // 64 + 2 x 1024 words, zeroed: 3 argmax slots 16 words apart,
+                                // then per-block covered-entry [64 + b] and queued-entry
+                                // [64 + 1024 + b] tallies
+  int64_t n_sets;               // N: sets [0, N) take part
+  unsigned long long total_entries;  // entries of those sets
   unsigned int* sync;           // 128 words, zeroed: count [0], release word (64-bit) [32],
                                 // timeout flag [64], chunk-queue lengths [96], [112]
   unsigned long long* chunk_q;  // (set, first member) of queued decrement chunks

@@ -142,6 +142,23 @@ def test_greedy_long_k_candidate_cache(model):
         assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
 
 
+def test_greedy_long_sets_queue_and_recount():
+    # every edge live on a 2^13-node R-MAT: sets are whole reverse-reachable
+    # sets, thousands of nodes sharing one core, so covering them goes through
+    # the queued-chunk path: the first pick recounts the gains, later ones drain
+    el = inputs.rmat(13, 1 << 16, seed=12)
+    thr = np.full(el.m, 0xFFFFFFFF, np.uint32)
+    og, gg = _pair(el, oracle.W_EXPLICIT, thr)
+    N = 3000
+    op, gp = _check_pool(og, gg, oracle.IC, seed=6, stream=0, N=N)
+    off, _ = op.arrays()
+    assert (np.diff(off) > 2 * 2048).sum() > 100
+    for k in (1, 5, 60):
+        os_, og_, oc = op.max_coverage(N, k)
+        gs_, gg_, gc = gp.max_coverage(N, k)
+        assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
+
+
 def test_greedy_flat_gains_ties():
     # an edgeless graph: every RR set is its root alone, gains are small and
     # heavily tied, so the smallest-id tie rule decides most picks
