@@ -369,7 +369,7 @@ def main():
         ach = abytes / (ks[dom]["ms"] / 1000.0) / 1e9
         # DRAM bytes per CTA-tier launch of one solve, from the ncu capture summarised in
         # profiles/sample_cta_dssa_ic_trivalency_rmat20.md (valid for this kernel build and workload)
-        traffic = 2.32e10 if (dom == "sample_cta" and name == DEFAULT) else None
+        traffic = 2.10e10 if (dom == "sample_cta" and name == DEFAULT) else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_source": peak_kind, "traffic": traffic,
                 "bytes_per_launch": abytes / max(1, ks[dom]["launches"]),

@@ -112,8 +112,9 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
  * best values depend on the graph (wide bimodal sets favour mid_cap 0; deep
  * chains favour 16384; hubs of millions of in-edges favour an early hand-over).
  * ssa_autotune times a pilot batch of pilot_samples sets (0 = 8192) under the
- * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never} and keeps
- * the fastest in the graph handle; a solve on an untuned graph tunes it first.
+ * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never}, after one
+ * untimed pass that sizes the pilot pool, and keeps the fastest in the graph
+ * handle; an IC solve on an untuned graph first tunes it on 4096 sets.
  * ssa_set_tuning fixes both by hand (0 <= mid_cap <= 16384, heavy_groups >= 1;
  * 0x7FFFFFFF = never hand over).  Results never depend on the tuning.  For
  * SSA_LT ssa_autotune has nothing to tune. */

@@ -794,41 +794,43 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
   const int cands[4][2] = {{0, 0x7FFFFFFF}, {mid_tier_max_cap(), 0x7FFFFFFF}, {0, 4096}, {mid_tier_max_cap(), 4096}};
   double best_ms = 1e300;
   int best = cands[1][0], best_heavy = cands[1][1];
-  for (const auto& cand : cands) {
-    const int c = cand[0];
-    Sampler S;
-    DevPool P;
-    ssa_status st = S.init(G, 0, nullptr, X);
-    S.mid_cap = c;
+  // One sampler and one pool serve every candidate: the tier settings are
+  // plain fields, and the pool keeps the capacity that an untimed first pass
+  // grew, so each timed pass samples the same pilot sets without re-runs.
+  Sampler S;
+  DevPool P;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ssa_status st = S.init(G, 0, nullptr, X);
+  if (st == SSA_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+    st = fail(SSA_E_CUDA, "autotune: cudaEventCreate failed");
+  for (int c = -1; c < 4 && st == SSA_OK; ++c) {
+    const auto& cand = cands[c < 0 ? 0 : c];
+    S.mid_cap = cand[0];
     S.heavy_groups = cand[1];
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    if (st == SSA_OK) {
-      // one untimed pass sizes the pool, the second is timed
-      st = S.append(P, 0x5EEDull, 0, pilot, X);
-      if (st == SSA_OK) {
-        P.release(X.st);
-        P = DevPool();
-        cudaEventRecord(a, X.st);
-        st = S.append(P, 0x5EEDull, 0, pilot, X);
-        cudaEventRecord(b, X.st);
-      }
-    }
+    P.count = 0;
+    P.entries = 0;
+    P.bounds.assign(1, {0, 0});
+    if (c >= 0) cudaEventRecord(a, X.st);
+    st = S.append(P, 0x5EEDull, 0, pilot, X);
+    if (st != SSA_OK || c < 0) continue;
+    cudaEventRecord(b, X.st);
     float ms = 0.f;
-    if (st == SSA_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    P.release(X.st);
-    S.release(X.st);
-    cudaStreamSynchronize(X.st);
-    if (st != SSA_OK) return st;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+      st = fail(SSA_E_CUDA, "autotune: event timing failed");
+      break;
+    }
     if (ms < best_ms) {
       best_ms = ms;
-      best = c;
+      best = cand[0];
       best_heavy = cand[1];
     }
   }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  P.release(X.st);
+  S.release(X.st);
+  cudaStreamSynchronize(X.st);
+  if (st != SSA_OK) return st;
   {
     std::lock_guard<std::mutex> lock(G->tune_mu);
     G->tuned_mid_cap = best;
@@ -922,7 +924,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
       std::lock_guard<std::mutex> lock(g->tune_mu);
       tuned = g->tuned_mid_cap >= 0;
     }
-    if (!tuned) TRY(autotune_ic(g, 8192, X, nullptr, nullptr));
+    if (!tuned) TRY(autotune_ic(g, 4096, X, nullptr, nullptr));
     X.launches = 0;
   }
   Sampler S;
