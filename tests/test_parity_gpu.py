@@ -136,7 +136,9 @@ def test_greedy_long_k_candidate_cache(model):
     og, gg = _pair(el)
     N = 40_000
     op, gp = _check_pool(og, gg, model, seed=3, stream=0, N=N)
-    for k in (9, 300, 3000):
+    # 20000 picks (the largest k the paper sweeps) run on past full coverage
+    # into zero-gain picks, which go by smallest id
+    for k in (9, 300, 3000, 20000):
         os_, og_, oc = op.max_coverage(N, k)
         gs_, gg_, gc = gp.max_coverage(N, k)
         assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
