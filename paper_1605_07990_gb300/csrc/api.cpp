@@ -11,6 +11,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ssa.h"
 #include "kernels.h"
 
@@ -114,6 +116,19 @@ struct ssa_graph {
 // per-stream execution context: kernel counting and optional event timing
 // ---------------------------------------------------------------------------
 namespace {
+// NVTX range for a profiler's timeline (a no-op unless a tool is attached);
+// ends when the scope does, error returns included
+struct NvtxRange {
+  nvtxRangeId_t id;
+  explicit NvtxRange(const char* name) : id(nvtxRangeStartA(name)) {}
+  ~NvtxRange() { nvtxRangeEnd(id); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+const char* const kClassName[SSA_K_COUNT] = {"ssa sample (warp tiers)", "ssa sample (CTA tier)", "ssa index",
+                                              "ssa greedy", "ssa stare"};
+
 struct Exec {
   cudaStream_t st = nullptr;
   int num_sms = 152;
@@ -136,16 +151,31 @@ struct Exec {
     cudaEventCreate(&e);
     return e;
   }
-  // begin/end a timed region of one kernel class
+  // begin/end a region of one kernel class: an NVTX range always, CUDA
+  // events when timing.  Regions are used LIFO; one left open by an error
+  // return stays on the list until collect().
+  struct Mark {
+    int ev;
+    nvtxRangeId_t nv;
+  };
+  std::vector<Mark> marks;
   int begin(int cls) {
-    if (!timing) return -1;
-    Ev e{cls, take(), take()};
-    cudaEventRecord(e.a, st);
-    evs.push_back(e);
-    return (int)evs.size() - 1;
+    Mark m{-1, nvtxRangeStartA(kClassName[cls])};
+    if (timing) {
+      Ev e{cls, take(), take()};
+      cudaEventRecord(e.a, st);
+      evs.push_back(e);
+      m.ev = (int)evs.size() - 1;
+    }
+    marks.push_back(m);
+    return (int)marks.size() - 1;
   }
   void end(int h) {
-    if (h >= 0) cudaEventRecord(evs[(size_t)h].b, st);
+    if (h < 0 || (size_t)h >= marks.size()) return;
+    const Mark m = marks[(size_t)h];
+    if (m.ev >= 0) cudaEventRecord(evs[(size_t)m.ev].b, st);
+    nvtxRangeEnd(m.nv);
+    if ((size_t)h + 1 == marks.size()) marks.pop_back();
   }
   void collect(ssa_kstat* ks) {
     for (auto& e : evs) {
@@ -158,6 +188,7 @@ struct Exec {
       spare.push_back(e.b);
     }
     evs.clear();
+    marks.clear();
   }
   ~Exec() {
     for (auto& e : evs) {
@@ -907,6 +938,7 @@ ssa_status check_params(const ssa_graph* g, const ssa_params* p) {
 
 ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
   const double t0 = now_s();
+  NvtxRange nv_solve(p && p->algo == SSA_ALGO_DSSA ? "ssa solve (D-SSA)" : "ssa solve (SSA)");
   const ssa_graph* g = sv->g;
   TRY(check_params(g, p));
   if (!out || !out->seeds) return fail(SSA_E_ARG, "result seeds buffer missing");
@@ -944,6 +976,9 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     const int64_t base = (int64_t)std::ceil(P.lambda);
     for (;;) {
       t += 1;
+      char rname[32];
+      std::snprintf(rname, sizeof(rname), "ssa round %d", (int)t);
+      NvtxRange nv_round(rname);
       const int64_t N = base << (t - 1);
       ssa_round rec{};
       rec.t = t;
