@@ -40,6 +40,25 @@ DEFAULT = "dssa_ic_trivalency_rmat20_m16M_k100"
 METRIC, UNIT = "RR sets/s", "RR sets/s"
 
 
+def replica_seed(rank: int, step: int) -> int:
+    """Philox seed of a timed step: each rank is an independent replica, so
+    ranks and steps never share a seed (warm-up steps use 10000 + w + 1000 rank)."""
+    return 1 + step + 1000 * rank
+
+
+def reduce_over_ranks(ms: float, counts, device) -> tuple:
+    """Job-level timing and totals over the process group: the slowest rank's
+    time and the sums of the per-rank counts (RR sets, edge visits, node visits)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in c.tolist()]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -309,7 +328,7 @@ def main():
     solver = P.Solver(g, stream=stream.cuda_stream)
 
     def seed_of(step):
-        return 1 + step + 1000 * rank
+        return replica_seed(rank, step)
 
     for w in range(args.warmup):
         solver.solve(algo, model, k, eps, delta, 10_000 + w + 1000 * rank)
@@ -337,12 +356,7 @@ def main():
     nv = sum(r.node_visits for r in results)
     launches = sum(r.kernel_launches for r in results)
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        c = torch.tensor([rr, ev, nv], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        rr_all, ev_all, nv_all = (float(x) for x in c.tolist())
+        ms_max, (rr_all, ev_all, nv_all) = reduce_over_ranks(ms, (rr, ev, nv), "cuda")
     else:
         ms_max, rr_all, ev_all, nv_all = ms, float(rr), float(ev), float(nv)
     value = rr_all / (ms_max / 1000.0)
