@@ -13,6 +13,8 @@
 - WRIS (Sec. 6.3.1): a root is never a zero-benefit node.
 - Algorithm 2 on random set systems equals a greedy that recomputes every
   marginal gain from scratch, with the smallest id winning ties.
+- Algorithm 3 stops at the first prefix of the stream whose hit count reaches
+  Lambda_2.
 """
 import numpy as np
 import pytest
@@ -212,3 +214,27 @@ def test_lt_running_sum_equal_to_draw_passes_on(orc, d, data, key):
     root = (keyed(orc, seed, ROOT, stream, j, 0)[0] * n) >> 32
     want = [root] if root != 0 or tail is None else [0, tail]
     assert orc.rr_set(g, orc.LT, seed, stream, j).tolist() == want
+
+
+@SETTINGS
+@given(small_graph(max_n=7, max_m=12), st.data(), keys, st.sampled_from([0, 1]))
+def test_estimate_inf_is_first_prefix_reaching_lambda2(orc, ng, data, key, model):
+    # Algorithm 3: T is the first prefix of the sample stream whose hit count
+    # reaches Lambda_2 (0 when T_max sets do not), computed here from the RR
+    # sets one by one
+    n, edges = ng
+    seed, stream, _ = key
+    src = np.array([u for u, _ in edges], np.int32)
+    dst = np.array([v for _, v in edges], np.int32)
+    g = orc.Graph(n, src, dst, orc.W_WC)
+    S = sorted(data.draw(st.sets(st.integers(0, n - 1), min_size=1, max_size=n)))
+    lam2 = data.draw(st.floats(0.5, 12.0))
+    t_max = data.draw(st.integers(1, 40))
+    T, hits, _ = orc.estimate_inf(g, model, seed, stream, np.array(S, np.int32), lam2, t_max)
+    cov, want_T = 0, 0
+    for j in range(t_max):
+        cov += bool(set(orc.rr_set(g, model, seed, stream, j).tolist()) & set(S))
+        if cov >= lam2:
+            want_T = j + 1
+            break
+    assert (T, hits) == (want_T, cov)
