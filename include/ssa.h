@@ -224,7 +224,9 @@ ssa_status ssa_pool_export(const ssa_pool* p, int64_t first, int64_t count, int6
 ssa_status ssa_pool_counts(ssa_pool* p, int64_t N, int32_t* cnt);
 /* Max-Coverage (Algorithm 2) over sets [0, N): k picks of largest marginal
  * gain, ties to the smallest id, seeds never re-picked.  seeds int32[k],
- * gains int64[k] (host); *cov = Cov_R(S). */
+ * gains int64[k] (host); *cov = Cov_R(S).  1 <= k <= n; N <= 2^31 - 2
+ * (SSA_E_ARG beyond).  All k picks run in one cooperative kernel; its grid
+ * barriers give up after about a second (SSA_E_TIMEOUT, never seen in use). */
 ssa_status ssa_max_coverage(ssa_pool* p, int64_t N, int32_t k, int32_t* seeds, int64_t* gains,
                             int64_t* cov);
 /* Cov (Eq. 1) of the host seed list over sets [first, first+count). */
