@@ -147,6 +147,8 @@ typedef struct {
   int64_t check_cov;         /* D-SSA: Cov_{R^c_t}(S_t); SSA: Estimate-Inf successes; -1 if not run */
   int64_t check_T;           /* SSA: Estimate-Inf T (0: T_max reached or not run) */
   double stat;               /* D-SSA: eps_t (-1 if D1 failed); SSA: I_c (-1 if none) */
+  double eps1, eps2, eps3;   /* D-SSA: the round's eps_1, eps_2, eps_3 of Algorithm 4 (-1 if D1
+                                failed); SSA: the fixed eps_1, eps_2, eps_3 of Eq. "set_ep" */
 } ssa_round;
 
 /* Kernel classes timed with CUDA events when ssa_result.kstats is requested. */

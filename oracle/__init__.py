@@ -42,7 +42,8 @@ class _Params(C.Structure):
 
 class _Round(C.Structure):
     _fields_ = [("t", C.c_int32), ("stop", C.c_int32), ("n_sets", C.c_int64), ("cov", C.c_int64),
-                ("check_cov", C.c_int64), ("check_T", C.c_int64), ("stat", C.c_double)]
+                ("check_cov", C.c_int64), ("check_T", C.c_int64), ("stat", C.c_double),
+                ("eps1", C.c_double), ("eps2", C.c_double), ("eps3", C.c_double)]
 
 
 class _Result(C.Structure):
@@ -260,5 +261,6 @@ def solve(g: Graph, algo, model, k, eps, delta, seed, benefit=None, max_rounds=6
     if t < 0:
         raise ValueError("oracle: bad solve arguments")
     trace = [{"t": r.t, "stop": r.stop, "n_sets": r.n_sets, "cov": r.cov, "check_cov": r.check_cov,
-              "check_T": r.check_T, "stat": r.stat} for r in tr[:min(t, max_rounds)]]
+              "check_T": r.check_T, "stat": r.stat, "eps1": r.eps1, "eps2": r.eps2, "eps3": r.eps3}
+             for r in tr[:min(t, max_rounds)]]
     return Solution(seeds, res.influence, res.rounds, res.n_rr, res.pool_entries, res.edge_visits, trace)

@@ -24,10 +24,14 @@
  *     (Algorithm 3); SSA (Algorithm 1, default parameters Eq. "set_ep");
  *     D-SSA (Algorithm 4); Upsilon (Table 1).
  *
- * Parity pins: see the header of each function.  The SSA / D-SSA drivers'
- * round-by-round decisions have no printed run in the paper to pin against:
- * "parity unpinned" for the exact round count and stop round; their final
- * guarantee (1-1/e-eps)*OPT is checked statistically on tiny graphs.
+ * Parity pins: see the header of each function.  The stopping rules are
+ * pinned round by round (tests/test_oracle_stop_rules.py): closed forms on an
+ * out-star whose every RR set holds the centre, the scale-free forms of
+ * Algorithm 4's eps_1, eps_2, eps_3, eps_t against Eq. "epsilon", and SSA's C2
+ * as a ratio of trace counts in cases where the choice of eps decides the
+ * round.  The exact round count on a random graph has no printed run in the
+ * paper to pin against ("parity unpinned" for it); the final guarantee
+ * (1-1/e-eps)*OPT is checked statistically on tiny graphs.
  *
  * Floating point: every FP64 decision is evaluated in the written order with
  * libm's log, sqrt, lgamma, ceil; build with -ffp-contract=off.
@@ -489,6 +493,8 @@ typedef struct {
   int64_t check_cov;     /* D-SSA: Cov_{R^c_t}(S_t); SSA: Estimate-Inf successes (-1: not run) */
   int64_t check_T;       /* SSA: Estimate-Inf T (0: T_max reached / not run) */
   double stat;           /* D-SSA: eps_t (or -1 when D1 failed); SSA: I_c (or -1) */
+  double eps1, eps2, eps3; /* D-SSA: the round's eps_1, eps_2, eps_3 (Algorithm 4; -1 when D1
+                              failed); SSA: the fixed eps_1, eps_2, eps_3 of Eq. set_ep */
 } orc_round;
 
 typedef struct {
@@ -533,8 +539,10 @@ int32_t orc_solve(const orc_graph* g, int algo, int model, int k, double eps, do
     orc_round rec;
     memset(&rec, 0, sizeof(rec));
     rec.t = t; rec.n_sets = N; rec.check_cov = -1; rec.check_T = 0; rec.stat = -1.0;
+    rec.eps1 = rec.eps2 = rec.eps3 = -1.0;
     int stop = 0;
     if (algo == 0) {
+      rec.eps1 = P.eps1; rec.eps2 = P.eps2; rec.eps3 = P.eps3;
       orc_pool_grow(pool, N);
       int64_t cov = orc_max_coverage(pool, N, k, S, gains);
       rec.cov = cov;
@@ -568,6 +576,7 @@ int32_t orc_solve(const orc_graph* g, int algo, int model, int k, double eps, do
         double e3 = eps * sqrt(scale * (1.0 + eps) * (ONE_MINUS_INV_E - eps) / ((1.0 + eps / 3.0) * pw * ic));
         double et = (e1 + e2 + e1 * e2) * (ONE_MINUS_INV_E - eps) + ONE_MINUS_INV_E * e3;
         rec.stat = et;
+        rec.eps1 = e1; rec.eps2 = e2; rec.eps3 = e3;
         if (et <= eps) stop = 1; /* condition D2 */
       }
     }

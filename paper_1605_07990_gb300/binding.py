@@ -37,7 +37,8 @@ class ssa_params(C.Structure):
 
 class ssa_round(C.Structure):
     _fields_ = [("t", C.c_int32), ("stop", C.c_int32), ("n_sets", C.c_int64), ("cov", C.c_int64),
-                ("check_cov", C.c_int64), ("check_T", C.c_int64), ("stat", C.c_double)]
+                ("check_cov", C.c_int64), ("check_T", C.c_int64), ("stat", C.c_double),
+                ("eps1", C.c_double), ("eps2", C.c_double), ("eps3", C.c_double)]
 
 
 class ssa_kstat(C.Structure):
@@ -239,7 +240,8 @@ def _result(k, trace_cap, want_kstats):
 
 def _unpack(r, seeds, tr):
     trace = [{"t": x.t, "stop": x.stop, "n_sets": x.n_sets, "cov": x.cov, "check_cov": x.check_cov,
-              "check_T": x.check_T, "stat": x.stat} for x in tr[:min(r.rounds, r.trace_cap)]]
+              "check_T": x.check_T, "stat": x.stat, "eps1": x.eps1, "eps2": x.eps2, "eps3": x.eps3}
+             for x in tr[:min(r.rounds, r.trace_cap)]]
     ks = {KERNEL_CLASSES[i]: {"launches": r.kstats[i].launches, "ms": r.kstats[i].ms} for i in range(5)}
     return Result(seeds.copy(), r.influence, r.rounds, r.n_rr, r.pool_entries, r.edge_visits, r.node_visits,
                   r.kernel_launches, r.seconds, r.cta_sets, r.cta_edge_visits, r.cta_node_visits,

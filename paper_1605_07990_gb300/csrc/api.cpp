@@ -986,8 +986,12 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
       rec.check_cov = -1;
       rec.check_T = 0;
       rec.stat = -1.0;
+      rec.eps1 = rec.eps2 = rec.eps3 = -1.0;
       int stop = 0;
       if (!dssa) {
+        rec.eps1 = P.eps1;
+        rec.eps2 = P.eps2;
+        rec.eps3 = P.eps3;
         if ((st = S.append(pool, p->seed, 0, N - pool.count, X)) != SSA_OK) break;
         int64_t cov = 0;
         if ((st = C.greedy(pool, N, k, seeds.data(), gains.data(), &cov, X)) != SSA_OK) break;
@@ -1034,6 +1038,9 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
                                                ((1.0 + p->eps / 3.0) * pw * ic));
           const double et = (e1 + e2 + e1 * e2) * (kOneMinusInvE - p->eps) + kOneMinusInvE * e3;
           rec.stat = et;
+          rec.eps1 = e1;
+          rec.eps2 = e2;
+          rec.eps3 = e3;
           if (et <= p->eps) stop = 1;  // condition D2
         }
       }
