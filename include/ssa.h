@@ -184,6 +184,7 @@ typedef struct {
   int64_t cta_stored_entries; /* pool entries that tier wrote (hit-test sets store none) */
   int64_t cta_stored_sets;   /* sets that tier wrote to the pool */
   int64_t draws;             /* Philox draws: IC 4-edge groups that needed coins, LT picks */
+  int64_t cta_draws;         /* the CTA tier's share of draws */
   int32_t mid_cap;           /* IC sampler hand-over size used (see ssa_autotune) */
   int32_t heavy_groups;      /* IC: in-list length (4-edge groups) above which warp tiers hand over */
   int64_t kernel_launches;   /* CUDA kernels this library launched for the solve */

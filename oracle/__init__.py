@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,6 +71,7 @@ def _load():
         "orc_pool_off": (vp, [vp]), "orc_pool_nodes": (vp, [vp]),
         "orc_pool_edge_visits": (i64, [vp]),
         "orc_rr_set": (i64, [vp, C.c_int, u64, u32, u64, vp, vp]),
+        "orc_sample_threads": (C.c_int, [vp, C.c_int, u64, u32, vp, u64, i64, C.c_int, vp, vp]),
         "orc_coverage": (i64, [vp, i64, i64, vp, C.c_int]),
         "orc_max_coverage": (i64, [vp, i64, C.c_int, vp, vp]),
         "orc_max_coverage_sets": (i64, [i64, i64, vp, vp, C.c_int, vp, vp]),
@@ -214,6 +215,19 @@ def rr_set(g: Graph, model, seed, stream, j, benefit=None) -> np.ndarray:
     out = np.zeros(g.n, dtype=np.int32)
     sz = _load().orc_rr_set(g.h, model, seed & 0xFFFFFFFFFFFFFFFF, stream, j, _p(pre), _p(out))
     return out[:sz].copy()
+
+
+def sample_threads(g: Graph, model, seed, stream, j0, count, threads, benefit=None):
+    """RR sets [j0, j0+count) of a stream over `threads` host threads by sample
+    range, counted not stored: (threads used, pool entries, edge visits)."""
+    pre = benefit_prefix(benefit)
+    ent = np.zeros(1, dtype=np.int64)
+    ev = np.zeros(1, dtype=np.int64)
+    used = _load().orc_sample_threads(g.h, model, seed & 0xFFFFFFFFFFFFFFFF, stream, _p(pre), int(j0), int(count),
+                                      int(threads), _p(ent), _p(ev))
+    if used < 0:
+        raise ValueError("oracle: bad sample_threads arguments")
+    return int(used), int(ent[0]), int(ev[0])
 
 
 def estimate_inf(g: Graph, model, seed, stream, S, lambda2, t_max, benefit=None):

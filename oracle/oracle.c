@@ -37,6 +37,7 @@
  * libm's log, sqrt, lgamma, ceil; build with -ffp-contract=off.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -340,6 +341,64 @@ int64_t orc_rr_set(const orc_graph* g, int model, uint64_t seed, uint32_t stream
   int64_t sz = rr_set(s, stream, j, out);
   sampler_free(s);
   return sz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The sampling phase over several host threads (the all-cores CPU           */
+/* baseline): samples [j0, j0+count) are split into contiguous ranges, one    */
+/* per thread, and each thread runs its own single-threaded sampler (the      */
+/* code above) over its range.  Sets are counted, not stored.  The RR sets    */
+/* are the same as one thread's: each is a function of its key alone.         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_graph* g;
+  int model;
+  uint64_t seed;
+  uint32_t stream;
+  const uint64_t* bprefix;
+  uint64_t j0, j1;
+  int64_t entries, edge_visits;
+} orc_range_job;
+
+static void* sample_range(void* arg) {
+  orc_range_job* a = (orc_range_job*)arg;
+  orc_sampler* s = sampler_new(a->g, a->model, a->seed, a->bprefix);
+  int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)a->g->n);
+  for (uint64_t j = a->j0; j < a->j1; ++j) a->entries += rr_set(s, a->stream, j, buf);
+  a->edge_visits = s->edge_visits;
+  free(buf);
+  sampler_free(s);
+  return NULL;
+}
+
+/* Returns the number of threads used (1..threads), or -1 on a bad argument. */
+int orc_sample_threads(const orc_graph* g, int model, uint64_t seed, uint32_t stream,
+                       const uint64_t* benefit_prefix, uint64_t j0, int64_t count, int threads,
+                       int64_t* entries, int64_t* edge_visits) {
+  if (count < 0 || threads < 1) return -1;
+  if (threads > count && count > 0) threads = (int)count;
+  orc_range_job* jobs = (orc_range_job*)calloc((size_t)threads, sizeof(orc_range_job));
+  pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+  int started = 0;
+  for (int t = 0; t < threads; ++t) {
+    jobs[t].g = g; jobs[t].model = model; jobs[t].seed = seed; jobs[t].stream = stream;
+    jobs[t].bprefix = benefit_prefix;
+    jobs[t].j0 = j0 + (uint64_t)(count * t / threads);
+    jobs[t].j1 = j0 + (uint64_t)(count * (t + 1) / threads);
+    if (pthread_create(&tid[t], NULL, sample_range, &jobs[t]) != 0) break;
+    ++started;
+  }
+  /* a range whose thread could not start runs here */
+  for (int t = started; t < threads; ++t) sample_range(&jobs[t]);
+  int64_t e = 0, v = 0;
+  for (int t = 0; t < threads; ++t) {
+    if (t < started) pthread_join(tid[t], NULL);
+    e += jobs[t].entries; v += jobs[t].edge_visits;
+  }
+  if (entries) *entries = e;
+  if (edge_visits) *edge_visits = v;
+  free(jobs); free(tid);
+  return started > 0 ? started : 1;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -50,7 +50,7 @@ class ssa_result(C.Structure):
                 ("influence", C.c_double), ("rounds", C.c_int32), ("n_rr", C.c_int64),
                 ("pool_entries", C.c_int64), ("edge_visits", C.c_int64), ("node_visits", C.c_int64),
                 ("cta_sets", C.c_int64), ("cta_edge_visits", C.c_int64), ("cta_node_visits", C.c_int64),
-                ("cta_stored_entries", C.c_int64), ("cta_stored_sets", C.c_int64), ("draws", C.c_int64),
+                ("cta_stored_entries", C.c_int64), ("cta_stored_sets", C.c_int64), ("draws", C.c_int64), ("cta_draws", C.c_int64),
                 ("mid_cap", C.c_int32), ("heavy_groups", C.c_int32),
                 ("kernel_launches", C.c_int64), ("seconds", C.c_double), ("want_kstats", C.c_int32),
                 ("kstats", ssa_kstat * 5)]
@@ -213,6 +213,7 @@ class Result:
     cta_stored_entries: int = 0
     cta_stored_sets: int = 0
     draws: int = 0
+    cta_draws: int = 0
     mid_cap: int = 0
     heavy_groups: int = 0
     trace: list = field(default_factory=list)
@@ -245,7 +246,7 @@ def _unpack(r, seeds, tr):
     ks = {KERNEL_CLASSES[i]: {"launches": r.kstats[i].launches, "ms": r.kstats[i].ms} for i in range(5)}
     return Result(seeds.copy(), r.influence, r.rounds, r.n_rr, r.pool_entries, r.edge_visits, r.node_visits,
                   r.kernel_launches, r.seconds, r.cta_sets, r.cta_edge_visits, r.cta_node_visits,
-                  r.cta_stored_entries, r.cta_stored_sets, r.draws, r.mid_cap, r.heavy_groups,
+                  r.cta_stored_entries, r.cta_stored_sets, r.draws, r.cta_draws, r.mid_cap, r.heavy_groups,
                   trace, ks)
 
 

@@ -263,15 +263,18 @@ struct Sampler {
   uint64_t* bprefix = nullptr;
   uint64_t wsum = 0;
   int lt_cumulative = 0;
+  int wc_implicit = 0;
   int mid_cap = 16384;  // IC: largest set the global warp tier keeps (0 = none)
   int heavy_groups = 0x7FFFFFFF;  // IC: warp tiers hand samples with longer in-lists to the CTA tier
   int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
   int64_t cta_edge_visits = 0, cta_node_visits = 0, cta_samples = 0;
   int64_t cta_store_nodes = 0, cta_store_sets = 0;  // the CTA tier's sets written to the pool
   int64_t draws = 0;  // Philox draws of IC edge groups / LT picks
+  int64_t cta_draws = 0;
 
   void tally(int64_t count) {
     draws += (int64_t)h_ctr->draws;
+    cta_draws += (int64_t)h_ctr->cta_draws;
     edge_visits += (int64_t)h_ctr->edge_visits;
     node_visits += (int64_t)h_ctr->node_visits;
     cta_edge_visits += (int64_t)h_ctr->cta_edge_visits;
@@ -284,6 +287,7 @@ struct Sampler {
     g = G->view();
     model = mdl;
     lt_cumulative = (mdl == 1 && G->weighting == SSA_W_EXPLICIT) ? 1 : 0;
+    wc_implicit = G->weighting == SSA_W_WC ? 1 : 0;
     {
       std::lock_guard<std::mutex> lock(G->tune_mu);
       if (G->tuned_mid_cap >= 0) {
@@ -349,6 +353,7 @@ struct Sampler {
     J.g = g;
     J.model = model;
     J.lt_cumulative = lt_cumulative;
+    J.wc_implicit = wc_implicit;
     J.seed = seed;
     J.stream = stream;
     J.j0 = j0;
@@ -445,6 +450,7 @@ struct Sampler {
       ev += h_ctr->edge_visits;
       nv += h_ctr->node_visits;
       draws += (int64_t)h_ctr->draws;
+      cta_draws += (int64_t)h_ctr->cta_draws;
       cev += h_ctr->cta_edge_visits;
       cnv += h_ctr->cta_node_visits;
       csets += h_ctr->big_count;
@@ -1072,6 +1078,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     out->cta_stored_entries = S.cta_store_nodes;
     out->cta_stored_sets = S.cta_store_sets;
     out->draws = S.draws;
+    out->cta_draws = S.cta_draws;
     out->mid_cap = p->model == SSA_IC ? S.mid_cap : 0;
     out->heavy_groups = p->model == SSA_IC ? S.heavy_groups : 0;
     out->kernel_launches = X.launches;

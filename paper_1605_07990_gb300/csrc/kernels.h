@@ -32,6 +32,7 @@ struct Counters {
   unsigned long long node_visits;  // nodes added to RR sets
   unsigned long long cta_edge_visits;  // the CTA tier's share of the two above
   unsigned long long cta_node_visits;
+  unsigned long long cta_draws;    // the CTA tier's share of draws
   unsigned long long draws;        // Philox draws (IC: one per 4-edge group that needed coins)
   unsigned long long ok_end;        // end of the last pool reservation that fit
   unsigned long long fail_count;    // samples whose reservation did not fit (listed in fail_list)
@@ -45,6 +46,8 @@ struct SampleJob {
   GraphView g;
   int model = 0;                 // 0 IC, 1 LT
   int lt_cumulative = 0;         // LT with explicit in-weights: pick by running threshold sums
+  int wc_implicit = 0;           // IC with weighted-cascade weights: thresholds from in-degrees,
+                                 // records read for live edges only
   uint64_t seed = 0;
   uint32_t stream = 0;
   int64_t j0 = 0, count = 0;     // samples [j0, j0+count), or work_list[0, count)

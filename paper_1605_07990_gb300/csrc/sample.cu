@@ -125,13 +125,34 @@ __device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u, uint32_t* s
 // handed to visit(u) in rounds of 32 (NO_NODE for idle lanes).  known(u) may
 // report tails already in the set so their edges need no draw.  Returns the
 // warp-uniform "stop" of visit.
-template <class Known, class Visit>
+template <bool WC, class Known, class Visit>
 __device__ __forceinline__ bool process_slab(const GraphView& g, bool valid, uint32_t grp, uint32_t olo, uint32_t ohi,
-                                             const uint32_t* rk, const SampleConst& sc, int lane, uint32_t* stage,
-                                             unsigned long long& draws, Known&& known, Visit&& visit) {
+                                             uint32_t othr, const uint32_t* rk, const SampleConst& sc, int lane,
+                                             uint32_t* stage, unsigned long long& draws, Known&& known,
+                                             Visit&& visit) {
   const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t cand = 0, u0 = 0, u1 = 0, u2 = 0, u3 = 0;
-  if (valid) {
+  if (WC && valid) {
+    // weighted cascade: every in-edge of the owner has threshold othr, so the
+    // coins need no record; only live edges load their tail
+    const uint32_t e = grp * 4u;
+    const uint32_t a = olo > e ? olo - e : 0u;
+    const uint32_t b = ohi - e;
+    const uint32_t need = (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
+    ++draws;
+    const uint4 r = philox_x(grp, sc, rk);
+    if ((need & 1u) && edge_live(r.x, othr)) cand |= 1u;
+    if ((need & 2u) && edge_live(r.y, othr)) cand |= 2u;
+    if ((need & 4u) && edge_live(r.z, othr)) cand |= 4u;
+    if ((need & 8u) && edge_live(r.w, othr)) cand |= 8u;
+    if (cand) {
+      const uint2* p = g.edge + (size_t)e;
+      if (cand & 1u) u0 = __ldg(&p[0].x);
+      if (cand & 2u) u1 = __ldg(&p[1].x);
+      if (cand & 4u) u2 = __ldg(&p[2].x);
+      if (cand & 8u) u3 = __ldg(&p[3].x);
+    }
+  } else if (valid) {
     const uint32_t e = grp * 4u;
     // edges e..e+3 that belong to the in-list
     const uint32_t a = olo > e ? olo - e : 0u;
@@ -186,14 +207,22 @@ __device__ __forceinline__ bool process_slab(const GraphView& g, bool valid, uin
 // take_heavy(...) == HEAVY_ABORT for some lane (the caller hands the sample on).
 constexpr int HEAVY_SKIP = 1, HEAVY_ABORT = 2;
 
-template <class Known, class Visit, class Heavy>
+// Weighted-cascade threshold of a node with d in-edges: floor(2^32 / d), and
+// 0xFFFFFFFF (probability 1) for d = 1.
+__device__ __forceinline__ uint32_t wc_threshold(uint32_t d) {
+  return d <= 1u ? 0xFFFFFFFFu : (uint32_t)(0x100000000ull / d);
+}
+
+template <bool WC, class Known, class Visit, class Heavy>
 __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
                                          int lane, uint32_t* stage, unsigned long long& ev, unsigned long long& draws,
                                          int heavy_groups, Known&& known, Visit&& visit, Heavy&& take_heavy) {
   uint32_t lo = 0, hi = 0;  // edge positions fit 32 bits (m < 2^31)
+  uint32_t thr = 0;
   if (v >= 0) {
     lo = (uint32_t)__ldg(g.off + v);
     hi = (uint32_t)__ldg(g.off + v + 1);
+    if (WC) thr = wc_threshold(hi - lo);
   }
   int ng = (hi > lo) ? (int)(((hi + 3) >> 2) - (lo >> 2)) : 0;
   int heavy = 0;
@@ -215,9 +244,10 @@ __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const ui
     owner = owner > 31 ? 31 : owner;
     const uint32_t olo = __shfl_sync(FULL_MASK, lo, owner);
     const uint32_t ohi = __shfl_sync(FULL_MASK, hi, owner);
+    const uint32_t othr = WC ? __shfl_sync(FULL_MASK, thr, owner) : 0u;
     const int oex = __shfl_sync(FULL_MASK, excl, owner);
     const uint32_t grp = (olo >> 2) + (uint32_t)(q - oex);
-    if (process_slab(g, q < total, grp, olo, ohi, rk, sc, lane, stage, draws, known, visit)) return 1;
+    if (process_slab<WC>(g, q < total, grp, olo, ohi, othr, rk, sc, lane, stage, draws, known, visit)) return 1;
   }
   return 0;
 }
@@ -233,6 +263,7 @@ __device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev
     if (nv) atomicAdd(&ctr->node_visits, nv);
     if (cta_tier && ev) atomicAdd(&ctr->cta_edge_visits, ev);
     if (cta_tier && nv) atomicAdd(&ctr->cta_node_visits, nv);
+    if (cta_tier && dr) atomicAdd(&ctr->cta_draws, dr);
   }
 }
 
@@ -269,7 +300,7 @@ __device__ __forceinline__ void warp_store_set(const SampleJob& J, int64_t j, co
   }
 }
 
-template <int MODE, int TIER>
+template <int MODE, int TIER, bool WC>
 __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
   constexpr int HBITS = Tier<TIER>::HBITS, QCAP = Tier<TIER>::QCAP;
   __shared__ __align__(16) uint32_t s_hash[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_HASH : 4];
@@ -339,7 +370,8 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) == 2) {
+      if (expand_ic<WC>(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
+          2) {
         handoff = true;
         break;
       }
@@ -470,7 +502,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
 // KIND 1: small CTAs (bitmap in global memory, queue of small_qcap entries);
 //         a set that outgrows the queue goes on to KIND 2.
 // KIND 2: full-size CTAs (global bitmap, queue of n entries) for those sets.
-template <int MODE, bool SMEM_BITMAP, int KIND>
+template <int MODE, bool SMEM_BITMAP, int KIND, bool WC>
 __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(SampleJob J) {
   constexpr int WARPS = KIND == 1 ? 8 : 32;
   extern __shared__ __align__(16) uint32_t s_bits[];
@@ -479,7 +511,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
   __shared__ unsigned long long s_pos;
   __shared__ uint32_t s_stage[WARPS][STAGE];
   // heavy in-lists of the current level, expanded by all warps together
-  __shared__ uint32_t s_hlo[CTA_HEAVY_CAP], s_hhi[CTA_HEAVY_CAP];
+  __shared__ uint32_t s_hlo[CTA_HEAVY_CAP], s_hhi[CTA_HEAVY_CAP], s_hthr[WC ? CTA_HEAVY_CAP : 1];
   __shared__ int s_hpref[CTA_HEAVY_CAP];
   __shared__ int s_nheavy, s_htotal, s_hnext;
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
@@ -546,6 +578,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
         if (slot >= CTA_HEAVY_CAP) return 0;  // list full: this warp expands it itself
         s_hlo[slot] = lo;
         s_hhi[slot] = hi;
+        if (WC) s_hthr[slot] = wc_threshold(hi - lo);
         ev += hi - lo;
         return HEAVY_SKIP;
       };
@@ -565,7 +598,8 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
           if (b >= lvl_end) break;
           const int cnt = min(32, lvl_end - b);
           const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
-          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy)) break;
+          if (expand_ic<WC>(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy))
+            break;
         }
         __syncthreads();
         const int nh = min(s_nheavy, CTA_HEAVY_CAP);
@@ -598,7 +632,9 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
               if (it + step < nh && s_hpref[it + step] <= q) it += step;
             const uint32_t olo = s_hlo[it], ohi = s_hhi[it];
             const uint32_t grp = (olo >> 2) + (uint32_t)(q - s_hpref[it]);
-            if (process_slab(J.g, q < htotal, grp, olo, ohi, J.rk, sc, lane, stage, dr, known, visit)) break;
+            if (process_slab<WC>(J.g, q < htotal, grp, olo, ohi, WC ? s_hthr[it] : 0u, J.rk, sc, lane, stage, dr,
+                                 known, visit))
+              break;
           }
         }
         __syncthreads();
@@ -705,7 +741,8 @@ LaunchCfg sampler_config(const GraphView& g, int model) {
   cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
   if (model == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE, 0>, WT_WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE, 0, false>, WT_WARPS * 32,
+                                                  0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_lt<MODE_STORE>, WT_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
@@ -718,7 +755,8 @@ LaunchCfg sampler_config(const GraphView& g, int model) {
   if (!c.cta_smem_bitmap) {
     // global bitmap: many small CTAs first, a few full-size ones for the largest sets
     int small_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, false>, 256,
+                                                  0);
     if (small_per_sm < 1) small_per_sm = 1;
     c.small_blocks = c.num_sms * small_per_sm;
     c.small_qcap = (int)std::min<int64_t>(g.n, 1 << 20);
@@ -739,15 +777,22 @@ size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c) {
   return per_slot * (size_t)c.cta_blocks + ((size_t)c.small_qcap * 4 + words * 4) * (size_t)c.small_blocks;
 }
 
+template <int MODE, bool WC>
+static void launch_warp_ic(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
+  const dim3 block(WT_WARPS * 32);
+  k_sample_warp_ic<MODE, 0, WC><<<c.warp_blocks, block, 0, st>>>(J);
+  if (J.mid_cap > 0) k_sample_warp_ic<MODE, 1, WC><<<c.mid_blocks, block, 0, st>>>(J);
+}
+
 cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
   const dim3 grid(c.warp_blocks), block(WT_WARPS * 32);
   if (J.model == 0) {
     if (J.mode == MODE_STORE) {
-      k_sample_warp_ic<MODE_STORE, 0><<<grid, block, 0, st>>>(J);
-      if (J.mid_cap > 0) k_sample_warp_ic<MODE_STORE, 1><<<c.mid_blocks, block, 0, st>>>(J);
+      if (J.wc_implicit) launch_warp_ic<MODE_STORE, true>(J, c, st);
+      else launch_warp_ic<MODE_STORE, false>(J, c, st);
     } else {
-      k_sample_warp_ic<MODE_HIT, 0><<<grid, block, 0, st>>>(J);
-      if (J.mid_cap > 0) k_sample_warp_ic<MODE_HIT, 1><<<c.mid_blocks, block, 0, st>>>(J);
+      if (J.wc_implicit) launch_warp_ic<MODE_HIT, true>(J, c, st);
+      else launch_warp_ic<MODE_HIT, false>(J, c, st);
     }
   } else {
     if (J.mode == MODE_STORE) k_sample_warp_lt<MODE_STORE><<<grid, block, 0, st>>>(J);
@@ -756,25 +801,32 @@ cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStrea
   return cudaGetLastError();
 }
 
-template <int MODE, bool SB>
+template <int MODE, bool SB, bool WC>
 static cudaError_t launch_cta_t(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
   if (SB) {
     const size_t smem = (size_t)c.smem_bitmap_bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_sample_cta<MODE, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sample_cta<MODE, true, 0, WC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sample_cta<MODE, true, 0><<<c.cta_blocks, c.cta_threads, smem, st>>>(J);
+    k_sample_cta<MODE, true, 0, WC><<<c.cta_blocks, c.cta_threads, smem, st>>>(J);
   } else {
-    k_sample_cta<MODE, false, 1><<<c.small_blocks, 256, 0, st>>>(J);
-    k_sample_cta<MODE, false, 2><<<c.cta_blocks, c.cta_threads, 0, st>>>(J);
+    k_sample_cta<MODE, false, 1, WC><<<c.small_blocks, 256, 0, st>>>(J);
+    k_sample_cta<MODE, false, 2, WC><<<c.cta_blocks, c.cta_threads, 0, st>>>(J);
   }
   return cudaGetLastError();
 }
 
+template <int MODE, bool SB>
+static cudaError_t launch_cta_w(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
+  // the LT walk reads no thresholds: one instantiation serves it
+  return (J.model == 0 && J.wc_implicit) ? launch_cta_t<MODE, SB, true>(J, c, st)
+                                         : launch_cta_t<MODE, SB, false>(J, c, st);
+}
+
 cudaError_t launch_sample_cta(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
   if (J.mode == MODE_STORE)
-    return c.cta_smem_bitmap ? launch_cta_t<MODE_STORE, true>(J, c, st) : launch_cta_t<MODE_STORE, false>(J, c, st);
-  return c.cta_smem_bitmap ? launch_cta_t<MODE_HIT, true>(J, c, st) : launch_cta_t<MODE_HIT, false>(J, c, st);
+    return c.cta_smem_bitmap ? launch_cta_w<MODE_STORE, true>(J, c, st) : launch_cta_w<MODE_STORE, false>(J, c, st);
+  return c.cta_smem_bitmap ? launch_cta_w<MODE_HIT, true>(J, c, st) : launch_cta_w<MODE_HIT, false>(J, c, st);
 }
 
 }  // namespace ssa

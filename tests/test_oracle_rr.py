@@ -168,3 +168,20 @@ def test_lt_general_weights_lemma1(orc, gi):
         est = p.coverage(0, N, S) / N
         assert within_chernoff(est, I / el.n, N), (S, I, est * el.n)
     assert d.sum() == el.m
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_threaded_sampling_equals_one_thread(orc, model):
+    # the all-cores CPU baseline splits sample ids into ranges over threads; every
+    # RR set is a function of its key, so totals equal one thread's pool
+    el = inputs.rmat(12, 1 << 15, seed=2)
+    g = orc.Graph.from_edges(el, orc.W_WC)
+    pool = orc.Pool(g, model, seed=9, stream=3).grow(1500)
+    off, _ = pool.arrays()
+    for threads in (1, 3, 8):
+        used, entries, ev = orc.sample_threads(g, model, 9, 3, 0, 1500, threads)
+        assert used == threads
+        assert entries == off[-1] and ev == pool.edge_visits
+    # a range that starts past 0
+    used, entries, _ = orc.sample_threads(g, model, 9, 3, 500, 1000, 4)
+    assert entries == off[1500] - off[500]
