@@ -1,21 +1,30 @@
-"""Benchmark: RR sets/s of full D-SSA solves on a resident synthetic R-MAT graph.
+"""Benchmark: RR sets/s of whole SSA / D-SSA solves on a resident synthetic R-MAT graph.
 
-One step = one complete D-SSA solve (Algorithm 4) on the GPU: RR sampling of
-every doubling round, node->set index, greedy Max-Coverage, the stare check
-and the host FP64 stopping rule.  Workload: directed R-MAT, 2^20 nodes, 2^24
-draws (a,b,c,d = 0.57,0.19,0.19,0.05; duplicates and self-loops removed), IC
-with trivalency weights, k=100, eps=0.1, delta=1/n; each step uses a fresh
-Philox seed.  value = RR sets generated / device time; e2e repeats the steps
-through the C ABI from pinned host edge arrays (graph upload and CSR build
-inside the timed region).
+One step = one complete solve on the GPU: RR sampling of every doubling round,
+the node->set index, greedy Max-Coverage, the stare check and the host FP64
+stopping rule.  Default workload (the billion-edge configuration): plain SSA
+(Algorithm 1), IC with weighted-cascade weights w = 1/d_in, directed R-MAT on
+2^25 nodes from 1.3e9 draws (a,b,c,d = 0.57,0.19,0.19,0.05; duplicates and
+self-loops removed: 1,263,509,823 edges), k=100, eps=0.1, delta=1/n; each step
+draws a fresh Philox seed.  The D-SSA trivalency workload on 2^20 nodes / 2^24
+draws is measured in the same run and reported under "extra".
 
---impl reference times the plain CPU oracle on a bounded sample of the same
-workload (the RR sets of the first samples of the solve's stream).
-Multi-GPU (torchrun): independent replicas, one per rank, weak scaling.
+value = RR sets generated / device time of the timed steps (inputs resident).
+e2e = the same metric through the C ABI from pinned host edge arrays: graph
+upload, device CSR build, solve and seeds back, every step.
+roofline = the dominant kernel class against its real bound (see roofline()).
+cpu_baseline = the oracle as it stands on the host cores: the sampling phase on
+one thread and over all cores (by sample range), then Max-Coverage and the
+stare count over the one-thread sample.
+
+--impl reference times the oracle on the host cores on a bounded sample of the
+same workload per step.  Multi-GPU (torchrun): independent replicas, one per
+rank (weak scaling).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -31,13 +40,39 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: (scale, m_draw, weighting, algo, model, k, eps)
+    "ssa_ic_wc_rmat25_m1.3G_k100": (25, 1_300_000_000, 0, 0, 0, 100, 0.1),
     "dssa_ic_trivalency_rmat20_m16M_k100": (20, 1 << 24, 1, 1, 0, 100, 0.1),
     "ssa_ic_wc_rmat14_m128K_k50": (14, 1 << 17, 0, 0, 0, 50, 0.1),
     "dssa_lt_wc_rmat23_m128M_k500": (23, 1 << 27, 0, 1, 1, 500, 0.05),
-    "ssa_ic_wc_rmat25_m1.3G_k100": (25, 1_300_000_000, 0, 0, 0, 100, 0.1),
+    # a tenth of the billion-edge graph, same model and weights: small enough for ncu captures
+    "ssa_ic_wc_rmat23_m128M_k100": (23, 1 << 27, 0, 0, 0, 100, 0.1),
 }
-DEFAULT = "dssa_ic_trivalency_rmat20_m16M_k100"
+DEFAULT = "ssa_ic_wc_rmat25_m1.3G_k100"
+EXTRA = "dssa_ic_trivalency_rmat20_m16M_k100"
 METRIC, UNIT = "RR sets/s", "RR sets/s"
+WEIGHTS = ["weighted-cascade", "trivalency"]
+
+# ALU roofline of the IC samplers.  Each coin comes from one Philox4x32-10 draw
+# per 4-edge group: 10 rounds of two 32x32->64 multiplies and two three-input
+# XORs, 40 thread instructions at least.  At one warp instruction per SM
+# sub-partition per clock (4 per SM) the GPU issues at most
+#   SMs x 4 x clock x 32 lanes / 40 draws per second.
+PHILOX_MIN_INSTR = 40
+
+# DRAM bytes per unit of work from ncu captures of the sampler kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload and kernel
+# class, valid only for the kernel sources they were taken on (hash of
+# csrc/sample.cu, csrc/device.cuh, csrc/kernels.h); any other build reports
+# traffic null.
+TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sample.cu", "device.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1605_07990_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def replica_seed(rank: int, step: int) -> int:
@@ -127,11 +162,108 @@ def make_graph_inputs(name):
     return el, weighting, algo, model, k, eps
 
 
-def cpu_baseline(el, weighting, model, seed, budget_s):
-    """The oracle as it stands, single-threaded: RR sets of the solve's stream for ~budget_s."""
+def sampler_model(weighting, model):
+    if model == 1:
+        return "lt"
+    return "ic_wc" if weighting == 0 else "ic_records"
+
+
+def roofline(kind, dom, ks, results, sm_count, clock_mhz, name, hbm_peak, hbm_kind):
+    """Roofline of the dominant kernel class.
+
+    The IC samplers draw one Philox4x32-10 per 4-edge group; with weighted-cascade
+    weights the coins need no edge record (thresholds follow from in-degrees)
+    and the kernel is bound by integer issue, so it is reported in draws/s
+    against PHILOX_MIN_INSTR.  Algorithmic bytes per unit (for the HBM side
+    figure): weighted cascade, 16 per visited node (two CSR offsets) + 8 per
+    live edge taken (one record; at least one per visited node but the root)
+    + 8 per stored pool entry + 12 per stored set + 1 per hit-tested set;
+    edge records (trivalency, explicit), 8 per examined in-edge instead of the
+    per-live-edge record."""
+    if dom not in ("sample_cta", "sample_warp") or kind == "lt" or ks[dom]["ms"] <= 0:
+        return None
+    cta = dom == "sample_cta"
+    draws = sum((r.cta_draws if cta else r.draws - r.cta_draws) for r in results)
+    ev = sum((r.cta_edge_visits if cta else r.edge_visits - r.cta_edge_visits) for r in results)
+    nv = sum((r.cta_node_visits if cta else r.node_visits - r.cta_node_visits) for r in results)
+    sets = sum((r.cta_sets if cta else r.n_rr - r.cta_sets) for r in results)
+    st_e = sum((r.cta_stored_entries if cta else r.pool_entries - r.cta_stored_entries) for r in results)
+    st_s = sum((r.cta_stored_sets if cta else r.trace[-1]["n_sets"] - r.cta_stored_sets) for r in results)
+    sec = ks[dom]["ms"] / 1000.0
+    peak = sm_count * 4 * clock_mhz * 1e6 * 32 / PHILOX_MIN_INSTR
+    ach = draws / sec
+    if kind == "ic_wc":
+        abytes = 16 * nv + 8 * max(nv - sets, 0) + 8 * st_e + 12 * st_s + max(sets - st_s, 0)
+    else:
+        abytes = 8 * ev + 16 * nv + 8 * st_e + 12 * st_s + max(sets - st_s, 0)
+    launches = max(1, ks[dom]["launches"])
+    tr = TRAFFIC.get((name, dom))
+    traffic = None
+    if tr and tr["src"] == kernel_source_hash():
+        traffic = tr["bytes_per_node_visit"] * nv / launches
+    return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Philox draws/s",
+            "frac": ach / peak,
+            "peak_source": f"derived: {sm_count} SMs x 4 issue slots x {clock_mhz:.0f} MHz x 32 lanes / "
+                           f"{PHILOX_MIN_INSTR} instructions per Philox4x32-10 draw",
+            "traffic": traffic, "avg_launch_ms": ks[dom]["ms"] / launches,
+            "draws_per_launch": draws / launches, "edge_visits_per_launch": ev / launches,
+            "hbm": {"algorithmic_bytes_per_launch": abytes / launches, "algorithmic_gbs": abytes / sec / 1e9,
+                    "peak_gbs": hbm_peak, "frac": abytes / sec / 1e9 / hbm_peak, "peak_source": hbm_kind}}
+
+
+def run_solves(P, solver, name, steps, warmup, seed_of, stream, torch):
+    scale, m_draw, weighting, algo, model, k, eps = WORKLOADS[name]
+    n = 1 << scale
+    delta = 1.0 / n
+    for w in range(warmup):
+        solver.solve(algo, model, k, eps, delta, 10_000 + w + seed_of(0) - 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    e0.record(stream)
+    for s in range(steps):
+        results.append(solver.solve(algo, model, k, eps, delta, seed_of(s), want_kstats=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return results, e0.elapsed_time(e1)
+
+
+def summarise(P, name, results, ms, sm_count, clock_mhz):
+    scale, m_draw, weighting, algo, model, k, eps = WORKLOADS[name]
+    sec = ms / 1000.0
+    rr = sum(r.n_rr for r in results)
+    stored = sum(r.trace[-1]["n_sets"] for r in results)
+    ks = {c: {"launches": sum(r.kstats[c]["launches"] for r in results),
+              "ms": sum(r.kstats[c]["ms"] for r in results)} for c in P.binding.KERNEL_CLASSES}
+    dom = max(ks, key=lambda c: ks[c]["ms"])
+    hbm_peak, hbm_kind = peaks()
+    roof = roofline(sampler_model(weighting, model), dom, ks, results, sm_count, clock_mhz, name, hbm_peak,
+                    hbm_kind)
+    return {
+        "value": rr / sec, "ms_per_step": ms / len(results),
+        "edge_visits_per_s": sum(r.edge_visits for r in results) / sec,
+        "node_visits_per_s": sum(r.node_visits for r in results) / sec,
+        "philox_draws_per_s": sum(r.draws for r in results) / sec,
+        "rr_sets_per_solve": rr / len(results),
+        # SSA's Estimate-Inf sets and D-SSA's final check half are sampled in hit-test mode
+        # (each RR set stops at its first seed) and not stored; they count as drawn
+        "rr_sets_stored_per_solve": stored / len(results),
+        "rr_sets_hit_tested_per_solve": (rr - stored) / len(results),
+        "rounds": [r.rounds for r in results], "kernel_ms": ks, "dominant": dom,
+        "gpu_launches": sum(r.kernel_launches for r in results), "roofline": roof,
+    }
+
+
+def cpu_baseline(el, weighting, model, k, seed, budget_s):
+    """The oracle as it stands on the host cores: the sampling phase of the step-0
+    solve's stream on one thread for about budget_s, the same number of sets per
+    thread over all cores (by sample range), then Max-Coverage (Algorithm 2) and
+    the stare count (Eq. 1) over the one-thread sample."""
     import oracle
     oracle.build()
+    t0 = time.perf_counter()
     og = oracle.Graph(el.n, el.src, el.dst, weighting, None, 1)
+    t_graph = time.perf_counter() - t0
     pool = oracle.Pool(og, model, seed, 0)
     t0 = time.perf_counter()
     count, chunk = 0, 4
@@ -139,11 +271,33 @@ def cpu_baseline(el, weighting, model, seed, budget_s):
         count += chunk
         pool.grow(count)
         chunk = min(chunk * 2, 64)
-    dt = time.perf_counter() - t0
-    return count, dt, pool.edge_visits
+    t_one = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    used, _, _ = oracle.sample_threads(og, model, seed, 0, count, count * cores, cores)
+    t_all = time.perf_counter() - t0
+    n_all = count * cores
+    t0 = time.perf_counter()
+    seeds, _, cov = pool.max_coverage(count, min(k, el.n))
+    t_greedy = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pool.coverage(0, count, seeds)
+    t_stare = time.perf_counter() - t0
+    return {"value": n_all / t_all, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": (f"sampling phase of the step-0 solve's stream: sets [{count}, {count + n_all}) over "
+                       f"{used} threads by sample range ({t_all:.1f} s); one thread: sets [0, {count}) "
+                       f"({t_one:.1f} s); Max-Coverage k={min(k, el.n)} and the stare count over those "
+                       f"{count} sets"),
+            "single_thread": {"value": count / t_one, "unit": UNIT, "cores": 1},
+            "phases_s": {"sample_1_thread": t_one, "sample_all_cores": t_all, "greedy_1_thread": t_greedy,
+                         "stare_1_thread": t_stare, "graph_build_1_thread": t_graph},
+            "sets_one_thread": count, "sets_all_cores": n_all}
 
 
 def run_reference(args):
+    """The oracle on the host cores, as it stands: per step, the sampling phase of
+    a solve's stream (Philox seed = step index + 1) for a bounded number of sets,
+    over all cores by sample range."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -152,25 +306,24 @@ def run_reference(args):
     import oracle
     oracle.build()
     og = oracle.Graph(el.n, el.src, el.dst, weighting, None, 1)
-    per_step = args.ref_sets
-    times, counts = [], []
+    cores = os.cpu_count() or 1
+    per_step = args.ref_sets if args.ref_sets > 0 else 64 * cores
+    times, used = [], 1
     for s in range(args.warmup + args.steps):
-        pool = oracle.Pool(og, model, 1 + s, 0)
         t0 = time.perf_counter()
-        pool.grow(per_step)
+        used, _, _ = oracle.sample_threads(og, model, 1 + s, 0, 0, per_step, cores)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
-            counts.append(per_step)
     total_t = sum(times)
-    value = sum(counts) / total_t
-    sample = (f"first {per_step} RR sets of the D-SSA stream (Philox seed = step index + 1) of the workload, "
-              f"sampling only, per step")
+    value = per_step * args.steps / total_t
+    sample = (f"first {per_step} RR sets of each step's solve stream (Philox seed = step index + 1), "
+              f"sampling phase only, {used} host threads by sample range")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": name, "n": el.n, "m": el.m, "k": k, "eps": eps},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -263,7 +416,7 @@ def run_serving(args):
                        "queries": len(qs), "arrival_rate_per_s": rate, "slots": args.slots},
             "server": {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                        "queries_per_s": len(qs) / t_live, "saturated_queries_per_s": len(qs) / t_sat,
-                       "answers_equal_to_sequential": same},
+                       "answers_equal_to_sequential": same, "saturated_answers": len(sat)},
             "sequential_dssa": fifo(svc_d), "sequential_plain_ssa": fifo(svc_s),
             "mean_service_ms": {"dssa": 1e3 * float(svc_d.mean()), "ssa": 1e3 * float(svc_s.mean())}}
     print(json.dumps(line), flush=True)
@@ -279,9 +432,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--extra-steps", type=int, default=5, help="steps of the D-SSA trivalency workload (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-sets", type=int, default=150)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="one-thread sampling time of the CPU baseline")
+    ap.add_argument("--ref-sets", type=int, default=0, help="RR sets per reference step (0: 64 per host core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sample-only", type=int, default=0,
                     help="profiling case: only sample this many RR sets of the workload into a pool")
@@ -309,6 +463,8 @@ def main():
     __graft_entry__.build()
     import paper_1605_07990_gb300 as P
 
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
     name = args.workload
     el, weighting, algo, model, k, eps = make_graph_inputs(name)
     delta = 1.0 / el.n
@@ -330,103 +486,89 @@ def main():
     def seed_of(step):
         return replica_seed(rank, step)
 
-    for w in range(args.warmup):
-        solver.solve(algo, model, k, eps, delta, 10_000 + w + 1000 * rank)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
     try:
-        gpu_id = torch.cuda.get_device_properties(local).uuid
+        gpu_id = props.uuid
         gpu_id = f"GPU-{gpu_id}" if not str(gpu_id).startswith("GPU-") else str(gpu_id)
     except Exception:
         gpu_id = local
+    # warm-up outside the clock sampler, then the timed steps with it
+    run_solves(P, solver, name, 0, args.warmup, seed_of, stream, torch)
+    if world > 1:
+        dist.barrier()
     clk = Clocks(gpu_id)
     clk.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    results = []
-    e0.record(stream)
-    for s in range(args.steps):
-        results.append(solver.solve(algo, model, k, eps, delta, seed_of(s), want_kstats=True))
-    e1.record(stream)
-    torch.cuda.synchronize()
+    results, ms = run_solves(P, solver, name, args.steps, 0, seed_of, stream, torch)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    clock_mhz = clocks.get("sm_mhz") or 2070.0
     rr = sum(r.n_rr for r in results)
     ev = sum(r.edge_visits for r in results)
     nv = sum(r.node_visits for r in results)
-    launches = sum(r.kernel_launches for r in results)
     if world > 1:
         ms_max, (rr_all, ev_all, nv_all) = reduce_over_ranks(ms, (rr, ev, nv), "cuda")
     else:
         ms_max, rr_all, ev_all, nv_all = ms, float(rr), float(ev), float(nv)
+    summ = summarise(P, name, results, ms, sm_count, clock_mhz)
     value = rr_all / (ms_max / 1000.0)
-
-    # roofline of the dominant kernel class (CUDA events inside the library, same stream)
-    ks = {c: {"launches": sum(r.kstats[c]["launches"] for r in results),
-              "ms": sum(r.kstats[c]["ms"] for r in results)} for c in P.binding.KERNEL_CLASSES}
-    dom = max(ks, key=lambda c: ks[c]["ms"])
-    cta_ev = sum(r.cta_edge_visits for r in results)
-    cta_nv = sum(r.cta_node_visits for r in results)
-    cta_sets = sum(r.cta_sets for r in results)
-    cta_st_e = sum(r.cta_stored_entries for r in results)
-    cta_st_s = sum(r.cta_stored_sets for r in results)
-    # algorithmic bytes of the CTA-tier sampler: 8 per examined in-edge ({src,thr} record), 16 per
-    # visited node (its two CSR offsets), 8 per stored pool entry (node, sample id), 12 per stored
-    # set (start, length), 1 per hit-tested set (its flag)
-    if dom == "sample_cta":
-        abytes = 8 * cta_ev + 16 * cta_nv + 8 * cta_st_e + 12 * cta_st_s + (cta_sets - cta_st_s)
-    else:
-        abytes = None
-    peak, peak_kind = peaks()
-    roof = None
-    if abytes is not None and ks[dom]["ms"] > 0:
-        ach = abytes / (ks[dom]["ms"] / 1000.0) / 1e9
-        # DRAM bytes per CTA-tier launch of one solve, from the ncu capture summarised in
-        # profiles/sample_cta_dssa_ic_trivalency_rmat20.md (valid for this kernel build and workload)
-        traffic = 2.10e10 if (dom == "sample_cta" and name == DEFAULT) else None
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_source": peak_kind, "traffic": traffic,
-                "bytes_per_launch": abytes / max(1, ks[dom]["launches"]),
-                "avg_launch_ms": ks[dom]["ms"] / max(1, ks[dom]["launches"])}
-
+    cfg = {"workload": name, "n": el.n, "m": el.m, "algo": "D-SSA" if algo else "SSA",
+           "model": "LT" if model else "IC", "weights": WEIGHTS[weighting], "k": k, "eps": eps, "delta": "1/n",
+           "parallelism": f"replicas{world}",
+           "l2": f"inputs larger than L2 (CSR {P.ssa_graph_info(g)[2] / 1e9:.2f} GB; RR pool several GB per solve)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": name, "n": el.n, "m": el.m, "algo": "D-SSA" if algo else "SSA",
-                       "model": "LT" if model else "IC",
-                       "weights": ["weighted-cascade", "trivalency"][weighting], "k": k, "eps": eps,
-                       "delta": "1/n", "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (CSR 137 MB; RR pool several GB per solve)"},
-            "edge_visits_per_s": ev_all / (ms_max / 1000.0), "node_visits_per_s": nv_all / (ms_max / 1000.0),
-            "philox_draws_per_edge_visit": sum(r.draws for r in results) / max(1, ev),
-            "rr_sets_per_solve": rr / args.steps, "rounds": [r.rounds for r in results],
-            "kernel_ms": ks, "gpu_launches": launches, "clocks": clocks, "roofline": roof}
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
+            "edge_visits_per_s": ev_all / (ms_max / 1000.0), "node_visits_per_s": nv_all / (ms_max / 1000.0)}
+    for key in ("philox_draws_per_s", "rr_sets_per_solve", "rr_sets_stored_per_solve",
+                "rr_sets_hit_tested_per_solve", "rounds", "kernel_ms", "gpu_launches"):
+        line[key] = summ[key]
+    line["clocks"] = clocks
+    line["roofline"] = summ["roofline"]
 
-    # end to end through the C ABI: pinned host edges -> graph upload/CSR build -> solve -> seeds to host
+    # end to end through the C ABI: pinned host edges -> graph upload + device CSR build -> solve -> seeds to host
     src_h = torch.from_numpy(el.src).pin_memory()
     dst_h = torch.from_numpy(el.dst).pin_memory()
     src_np, dst_np = src_h.numpy(), dst_h.numpy()
     torch.cuda.synchronize()
+    rr_e2e, t_load, t_solve = 0, 0.0, 0.0
     t0 = time.perf_counter()
-    rr_e2e = 0
     for s in range(args.e2e_steps):
+        ta = time.perf_counter()
         g2 = P.ssa_load_graph(el.n, src_np, dst_np, None, weighting, 1)
+        tb = time.perf_counter()
         r = P.ssa_solve(g2, algo, model, k, eps, delta, 500 + seed_of(s))
+        tc = time.perf_counter()
         rr_e2e += r.n_rr
         g2.free()
+        t_load += tb - ta
+        t_solve += tc - tb
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    line["e2e"] = {"value": rr_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(el.m * 8),
-                   "d2h_bytes_per_step": int(k * 4 + 64), "steps": args.e2e_steps,
-                   "includes": "graph upload + device CSR build + solve + seeds to host"}
+    if args.e2e_steps > 0:
+        line["e2e"] = {"value": rr_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(el.m * 8),
+                       "d2h_bytes_per_step": int(k * 4 + 64), "steps": args.e2e_steps,
+                       "includes": "graph upload + device CSR build + solve (first solve on a new graph handle "
+                                   "runs the sampler autotuner) + seeds to host",
+                       "load_s_per_step": t_load / args.e2e_steps, "solve_s_per_step": t_solve / args.e2e_steps}
+
+    if args.extra_steps > 0 and name != EXTRA:
+        el2, w2, _, _, _, _ = make_graph_inputs(EXTRA)
+        g3 = P.ssa_load_graph(el2.n, el2.src, el2.dst, None, w2, 1)
+        solver3 = P.Solver(g3, stream=stream.cuda_stream)
+        res3, ms3 = run_solves(P, solver3, EXTRA, args.extra_steps, 2, seed_of, stream, torch)
+        ex = summarise(P, EXTRA, res3, ms3, sm_count, clock_mhz)
+        ex["config"] = {"n": el2.n, "m": el2.m, "algo": "D-SSA", "model": "IC", "weights": "trivalency", "k": 100,
+                        "eps": 0.1, "delta": "1/n", "l2": "CSR 137 MB: mostly L2-resident"}
+        ex["steps"] = args.extra_steps
+        line["extra"] = {EXTRA: ex}
+        solver3.free()
+        g3.free()
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        cnt, dt, cev = cpu_baseline(el, weighting, model, seed_of(0), args.cpu_seconds)
-        line["cpu_baseline"] = {"value": cnt / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {cnt} RR sets of the step-0 solve's stream, sampling only "
-                                          f"({dt:.1f} s single-threaded)"}
+        line["cpu_baseline"] = cpu_baseline(el, weighting, model, k, seed_of(0), args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    solver.free()
     g.free()
     if world > 1:
         dist.destroy_process_group()

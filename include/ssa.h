@@ -75,8 +75,13 @@ const char* ssa_status_str(ssa_status s);
 /* Copies the calling thread's last error message (NUL-terminated, truncated
  * to len) into buf.  Returns SSA_OK. */
 ssa_status ssa_last_error(char* buf, size_t len);
-/* Library version string, e.g. "ssa-gb300 0.1 sm_103a". */
+/* Library version string, e.g. "ssa-gb300 0.2 sm_103a". */
 const char* ssa_version(void);
+/* Architecture of the device code the CUDA runtime loaded for this library on
+ * the current device, as major*10 + minor (103 for sm_103a SASS): *binary from
+ * cudaFuncGetAttributes' binaryVersion, *ptx its ptxVersion.  Needs a GPU;
+ * SSA_E_CUDA when no device code fits the device. */
+ssa_status ssa_device_code_version(int32_t* binary, int32_t* ptx);
 
 /* ------------------------------------------------------------------------ */
 /* Graph store (Sec. 2: G = (V, E, w)).                                     */
@@ -97,6 +102,24 @@ const char* ssa_version(void);
 ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
                           const uint32_t* thr, ssa_weighting weighting, uint64_t weight_seed,
                           ssa_graph** out);
+/* Generate a directed R-MAT graph (Chakrabarti, Zhan, Faloutsos, SDM 2004) on
+ * the device and build its CSR there: the synthetic stand-in for the paper's
+ * networks (Sec. 6.1), without a host edge list or an upload.
+ *   scale        n = 2^scale nodes, 1 <= scale <= 30
+ *   m_draw       edges drawn, 0 <= m_draw < 2^31; self-loops and duplicate
+ *                (src, dst) pairs are removed, ssa_graph_info reports the rest
+ *   a, b, c      quadrant probabilities (d = 1 - a - b - c), each >= 0; each
+ *                level takes a 32-bit draw u and compares it with
+ *                floor(2^32 a), floor(2^32 (a+b)), floor(2^32 (a+b+c))
+ *   seed         key of the draws: level l of draw i uses the low (l even) or
+ *                high (l odd) half of SplitMix64 output number 32 i + l/2
+ *                (Steele, Lea, Flood, OOPSLA 2014), most significant bit first;
+ *                no noise and no id permutation
+ *   weighting    SSA_W_WC or SSA_W_TRIVALENCY (weight_seed keys the latter)
+ * The result equals ssa_load_graph of the same edge list.  Errors: SSA_E_ARG,
+ * SSA_E_NOMEM (the sort needs about 16 bytes per draw), SSA_E_CUDA. */
+ssa_status ssa_gen_rmat(int32_t scale, int64_t m_draw, double a, double b, double c, uint64_t seed,
+                        ssa_weighting weighting, uint64_t weight_seed, ssa_graph** out);
 ssa_status ssa_free_graph(ssa_graph* g);
 /* n, m and device bytes held by the graph (any pointer may be NULL). */
 ssa_status ssa_graph_info(const ssa_graph* g, int64_t* n, int64_t* m, int64_t* device_bytes);
@@ -121,6 +144,15 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
 ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_samples, int32_t* mid_cap,
                         double* pilot_ms);
 ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap, int32_t heavy_groups);
+
+/* Process-wide bound on the polls of each device-side wait: the grid barriers
+ * of the greedy kernel (ssa_max_coverage and every solve).  A wait that reaches
+ * it gives up, its kernel returns, and the call reports SSA_E_TIMEOUT.  polls
+ * >= 1 sets the bound (each poll backs off up to 128 ns); 0 restores the
+ * default of 2^22 polls, about a second.  Meant for failure handling and its
+ * tests: a small bound makes ordinary barriers give up.  Applies to launches
+ * after the call; SSA_E_ARG for polls < 0. */
+ssa_status ssa_set_wait_polls(int64_t polls);
 
 /* ------------------------------------------------------------------------ */
 /* Solve (Definition 1: IM; Algorithm 1 SSA; Algorithm 4 D-SSA).            */
@@ -228,8 +260,10 @@ ssa_status ssa_pool_counts(ssa_pool* p, int64_t N, int32_t* cnt);
 /* Max-Coverage (Algorithm 2) over sets [0, N): k picks of largest marginal
  * gain, ties to the smallest id, seeds never re-picked.  seeds int32[k],
  * gains int64[k] (host); *cov = Cov_R(S).  1 <= k <= n; N <= 2^31 - 2
- * (SSA_E_ARG beyond).  All k picks run in one cooperative kernel; its grid
- * barriers give up after about a second (SSA_E_TIMEOUT, never seen in use). */
+ * (SSA_E_ARG beyond).  All k picks run in one cooperative kernel; a wait at
+ * its grid barriers gives up after a bounded number of polls (about a second
+ * by default, see ssa_set_wait_polls): every block then returns and the call
+ * reports SSA_E_TIMEOUT, leaving the CUDA context usable. */
 ssa_status ssa_max_coverage(ssa_pool* p, int64_t N, int32_t k, int32_t* seeds, int64_t* gains,
                             int64_t* cov);
 /* Cov (Eq. 1) of the host seed list over sets [first, first+count). */
@@ -300,13 +334,15 @@ ssa_status ssa_server_destroy(ssa_server* s);
  *   stream   cudaStream_t to run on (NULL = the legacy default stream); the
  *            call synchronises that stream before returning.
  * Limit: n/32 + count/32 32-bit words plus a 256-byte header must fit the
- * 16 MiB array (n + count below about 134 million), else SSA_E_ARG.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * once, so make that first call before any stream capture.  Every call shares
- * the one array and clears the part it uses; calls that overlap on the GPU
- * (other streams, other host threads) race on it and must be serialised by
- * the caller.  Errors: SSA_E_ARG (sizes, null pointers, ids outside [0, n)),
- * SSA_E_CUDA. */
+ * 16 MiB array (n + count below about 134 million), else SSA_E_ARG.  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress) and is synchronous: it copies the count to the host
+ * and synchronises `stream` before returning, so it must not be called while
+ * that stream is being captured into a CUDA graph.  Every call shares the one
+ * array and clears the part it uses; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  Errors: SSA_E_ARG (sizes, null pointers, ids outside [0, n): the
+ * device checks every id and skips any outside), SSA_E_CUDA. */
 ssa_status ssa_coverage_noalloc(int64_t n, const int32_t* nodes, const int32_t* samp, int64_t entries,
                                 int64_t first, int64_t count, const int32_t* seeds, int32_t k,
                                 int64_t* cov, void* stream);

@@ -66,13 +66,17 @@ EXPORTS = {
     "ssa_status_str": (C.c_char_p, [C.c_int]),
     "ssa_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
     "ssa_version": (C.c_char_p, []),
+    "ssa_device_code_version": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ssa_load_graph": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_uint64,
                                  C.POINTER(C.c_void_p)]),
+    "ssa_gen_rmat": (C.c_int, [C.c_int32, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_int,
+                               C.c_uint64, C.POINTER(C.c_void_p)]),
     "ssa_free_graph": (C.c_int, [C.c_void_p]),
     "ssa_graph_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssa_graph_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssa_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "ssa_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "ssa_set_wait_polls": (C.c_int, [C.c_int64]),
     "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "ssa_solver_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
@@ -137,6 +141,13 @@ def ssa_version() -> str:
     return lib().ssa_version().decode()
 
 
+def ssa_device_code_version():
+    """(binary, ptx) architecture of the loaded device code, e.g. (103, 103)."""
+    b, p = C.c_int32(), C.c_int32()
+    _check(lib().ssa_device_code_version(C.byref(b), C.byref(p)))
+    return b.value, p.value
+
+
 # ---- graph ----
 class Graph:
     """Opaque device-resident graph handle (ssa_graph*)."""
@@ -166,6 +177,16 @@ def ssa_load_graph(n, src, dst, thr=None, weighting=SSA_W_WC, weight_seed=1) -> 
     return Graph(h.value, int(n), int(src.shape[0]))
 
 
+def ssa_gen_rmat(scale, m_draw, a=0.57, b=0.19, c=0.19, seed=1, weighting=SSA_W_WC, weight_seed=1) -> Graph:
+    """Directed R-MAT graph generated and built on the device."""
+    h = C.c_void_p()
+    _check(lib().ssa_gen_rmat(int(scale), int(m_draw), float(a), float(b), float(c), _u64(seed), int(weighting),
+                              _u64(weight_seed), C.byref(h)))
+    n, m = C.c_int64(), C.c_int64()
+    _check(lib().ssa_graph_info(h.value, C.byref(n), C.byref(m), None))
+    return Graph(h.value, n.value, m.value)
+
+
 def ssa_free_graph(g: Graph):
     g.free()
 
@@ -193,6 +214,11 @@ def ssa_autotune(g: Graph, model=SSA_IC, pilot_samples=0):
 
 def ssa_set_tuning(g: Graph, mid_cap, heavy_groups=0x7FFFFFFF):
     _check(lib().ssa_set_tuning(g.h, int(mid_cap), int(heavy_groups)))
+
+
+def ssa_set_wait_polls(polls=0):
+    """Bound the polls of every device-side wait (0 = the default, about a second)."""
+    _check(lib().ssa_set_wait_polls(int(polls)))
 
 
 # ---- solve ----

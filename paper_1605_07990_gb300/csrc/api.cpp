@@ -1,6 +1,7 @@
 // C ABI of libssa (include/ssa.h) and the host side of the Stop-and-Stare
 // drivers: device workspaces, sampling batches, and the FP64 stopping rules of
 // SSA (Algorithm 1) and D-SSA (Algorithm 4) evaluated from integer counts.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -75,6 +76,12 @@ ssa_status dev_grow(T** p, int64_t* cap, int64_t want, int64_t keep, cudaStream_
 }
 
 }  // namespace
+
+namespace {
+std::atomic<long long> g_wait_polls{GREEDY_DEFAULT_WAIT_POLLS};
+}  // namespace
+
+long long ssa::greedy_wait_polls() { return g_wait_polls.load(std::memory_order_relaxed); }
 
 // Lets other translation units of the library report an error message.
 void ssa::set_last_error(const char* msg) {
@@ -711,6 +718,7 @@ struct Cover {
     J.hist = hist;
     J.cache = cache;
     J.cache_n = hist + 2 * 4096;
+    J.wait_polls = greedy_wait_polls();
     int blocks = 0;
     // one cooperative greedy grid on the device at a time (solvers on other
     // host threads, e.g. serving slots, wait here)
@@ -1123,7 +1131,16 @@ ssa_status ssa_last_error(char* buf, size_t len) {
   return SSA_OK;
 }
 
-const char* ssa_version(void) { return "ssa-gb300 0.1 sm_103a"; }
+const char* ssa_version(void) { return "ssa-gb300 0.2 sm_103a"; }
+
+ssa_status ssa_device_code_version(int32_t* binary, int32_t* ptx) {
+  if (!binary || !ptx) return fail(SSA_E_ARG, "null output");
+  int b = 0, p = 0;
+  CU(device_code_version(&b, &p));
+  *binary = b;
+  *ptx = p;
+  return SSA_OK;
+}
 
 ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const uint32_t* thr,
                           ssa_weighting weighting, uint64_t weight_seed, ssa_graph** out) {
@@ -1198,6 +1215,51 @@ ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_
   return SSA_OK;
 }
 
+namespace {
+// a probability as a 32-bit threshold: floor(p 2^32), clamped to [0, 2^32 - 1]
+uint32_t prob_threshold(double p) {
+  if (!(p > 0.0)) return 0u;
+  const double x = p * 4294967296.0;
+  return x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+}
+}  // namespace
+
+ssa_status ssa_gen_rmat(int32_t scale, int64_t m_draw, double a, double b, double c, uint64_t seed,
+                        ssa_weighting weighting, uint64_t weight_seed, ssa_graph** out) {
+  if (!out) return fail(SSA_E_ARG, "null output handle");
+  *out = nullptr;
+  if (scale < 1 || scale > 30) return fail(SSA_E_ARG, "scale must lie in [1, 30]");
+  if (m_draw < 0 || m_draw > 0x7FFFFFFF) return fail(SSA_E_ARG, "m_draw must lie in [0, 2^31 - 1]");
+  if (!(a >= 0.0 && b >= 0.0 && c >= 0.0 && a + b + c <= 1.0))
+    return fail(SSA_E_ARG, "quadrant probabilities must be >= 0 with a + b + c <= 1");
+  if (weighting != SSA_W_WC && weighting != SSA_W_TRIVALENCY)
+    return fail(SSA_E_ARG, "ssa_gen_rmat weights: SSA_W_WC or SSA_W_TRIVALENCY");
+  cudaStream_t st;
+  CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  ssa_graph* g = new ssa_graph();
+  cudaGetDevice(&g->device);
+  g->n = int64_t(1) << scale;
+  g->weighting = weighting;
+  int launches = 0;
+  int64_t m = 0;
+  cudaError_t e = rmat_graph(scale, m_draw, prob_threshold(a), prob_threshold(a + b), prob_threshold(a + b + c), seed,
+                             (int)weighting, weight_seed, &m, &g->off, &g->edge, st, &launches);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (g->off) cudaFree(g->off);
+    if (g->edge) cudaFree(g->edge);
+    delete g;
+    return fail(e == cudaErrorMemoryAllocation ? SSA_E_NOMEM : SSA_E_CUDA, "R-MAT generation: %s",
+                cudaGetErrorString(e));
+  }
+  g->m = m;
+  g->bytes = (int64_t)(sizeof(int64_t) * (size_t)(g->n + 1) + sizeof(uint2) * (size_t)(((m + 3) / 4) * 4 + 4));
+  *out = g;
+  return SSA_OK;
+}
+
 ssa_status ssa_free_graph(ssa_graph* g) {
   if (!g) return SSA_OK;
   cudaDeviceSynchronize();
@@ -1261,6 +1323,12 @@ ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_sampl
   if (st != SSA_OK) return st;
   if (mid_cap) *mid_cap = chosen;
   if (pilot_ms) *pilot_ms = ms;
+  return SSA_OK;
+}
+
+ssa_status ssa_set_wait_polls(int64_t polls) {
+  if (polls < 0) return fail(SSA_E_ARG, "polls must be >= 0");
+  g_wait_polls.store(polls == 0 ? GREEDY_DEFAULT_WAIT_POLLS : (long long)polls, std::memory_order_relaxed);
   return SSA_OK;
 }
 

@@ -165,11 +165,12 @@ constexpr int ACC_DONE = 64, ACC_QUEUED = 64 + 1024;
 // (all its threads; f sees every block's writes from before the barrier) and
 // publishes the result (< 2^63) in the release word beside a sense bit (bit 0,
 // flipped by each release), so every waiter learns it from the poll that
-// releases it; all threads get it in `info`.  A wait gives up after about a
-// second, sets sync[SYNC_ERR] and returns false; that block then leaves the
-// kernel, and the others give up at their next barrier, which it never reaches.
+// releases it; all threads get it in `info`.  A wait gives up after `limit`
+// polls (about a second by default), sets sync[SYNC_ERR] and returns false;
+// that block then leaves the kernel, and the others give up at their next
+// barrier, which it never reaches.
 template <class F>
-__device__ __forceinline__ bool grid_barrier(unsigned int* sync, F&& f, unsigned long long& info) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* sync, long long limit, F&& f, unsigned long long& info) {
   __shared__ unsigned long long s_info;
   __shared__ unsigned int s_last, s_ok, s_sense;
   volatile unsigned long long* gw = reinterpret_cast<volatile unsigned long long*>(sync + SYNC_GEN);
@@ -196,7 +197,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* sync, F&& f, unsigned
     unsigned long long w;
     unsigned int ns = 8;
     for (long long spins = 0; (unsigned int)((w = *gw) & 1ull) == s_sense; ++spins) {
-      if (spins > (1ll << 22)) {  // seconds: a barrier never takes that long
+      if (spins > limit) {  // by default seconds: a barrier never takes that long
         atomicExch(sync + SYNC_ERR, 1u);
         s_ok = 0;
         break;
@@ -247,7 +248,7 @@ __device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long lo
   n_argmax += 1;
   unsigned long long* at = J.argmax + slot * ARGMAX_STRIDE;
   if (threadIdx.x == 0 && best != 0ull) atomicMax(at, best);
-  if (!grid_barrier(J.sync, [&] { return __ldcg(at); }, best)) return false;
+  if (!grid_barrier(J.sync, J.wait_polls, [&] { return __ldcg(at); }, best)) return false;
   if (blockIdx.x == 0 && threadIdx.x == 0) J.argmax[((slot + 2) % 3) * ARGMAX_STRIDE] = 0ull;
   return true;
 }
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         J.argmax[ACC_QUEUED + blockIdx.x] = my_queued;
       }
     }
-    if (!grid_barrier(J.sync, [&]() -> unsigned long long {
+    if (!grid_barrier(J.sync, J.wait_polls, [&]() -> unsigned long long {
           const unsigned int m = __ldcg(chunks);
           if (m > 0u) {
             // entries still in uncovered sets after this pick, against the queued ones
@@ -557,14 +558,14 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         reinterpret_cast<int4*>(J.cnt)[q] = c;
       }
       unsigned long long unused = 0;
-      if (!grid_barrier(J.sync, [] { return 0ull; }, unused)) return;
+      if (!grid_barrier(J.sync, J.wait_polls, [] { return 0ull; }, unused)) return;
       for (int64_t j = warp; j < J.n_sets; j += nwarps) {
         if (__ldcg(J.covered + j)) continue;
         const int32_t* mem = J.pool_nodes + J.set_start[j];
         const int32_t len = J.set_len[j];
         for (int t = lane; t < len; t += 32) atomicAdd(J.cnt + __ldg(mem + t), 1);
       }
-      if (!grid_barrier(J.sync, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
+      if (!grid_barrier(J.sync, J.wait_polls, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
     } else if (pay & PENDING) {
       const int64_t nchunks = (int64_t)(pay & (RECOUNT - 1ull));
       for (int64_t c = warp; c < nchunks; c += nwarps) {
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         const int32_t cnt = min(DEC_CHUNK, len - from);
         decrement_members(J.cnt, J.pool_nodes + J.set_start[j] + from, cnt, lane);
       }
-      if (!grid_barrier(J.sync, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
+      if (!grid_barrier(J.sync, J.wait_polls, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
     }
     fused_key = pay;
     fused_ok = fuse;
@@ -748,6 +749,15 @@ cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int*
   GreedyJob j = J;
   void* args[] = {&j};
   return cudaLaunchCooperativeKernel((const void*)k_greedy, dim3(blocks), dim3(1024), args, 0, st);
+}
+
+cudaError_t device_code_version(int* binary, int* ptx) {
+  cudaFuncAttributes a{};
+  const cudaError_t e = cudaFuncGetAttributes(&a, k_greedy);
+  if (e != cudaSuccess) return e;
+  *binary = a.binaryVersion;
+  *ptx = a.ptxVersion;
+  return cudaSuccess;
 }
 
 cudaError_t launch_add_counts(int32_t* total, const int32_t* add, int64_t n, cudaStream_t st, int num_sms) {

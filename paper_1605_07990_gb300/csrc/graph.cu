@@ -3,7 +3,10 @@
 // device radix sort (CUB, header source from the CUDA toolkit); offsets come
 // from segment boundaries of the sorted keys, thresholds from the weighting
 // rule: weighted cascade w = 1/d_in(v) (Sec. 6.1), trivalency, or explicit.
+#include <algorithm>
+
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_select.cuh>
 
 #include "device.cuh"
 
@@ -56,6 +59,38 @@ __global__ void k_fill_edges(const unsigned long long* keys, const int32_t* vals
   }
 }
 
+// SplitMix64's output function (Steele, Lea, Flood, OOPSLA 2014) applied to
+// a counter: draw number ctr of the stream keyed by seed.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
+  uint64_t z = seed + (ctr + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// R-MAT (Chakrabarti, Zhan, Faloutsos, SDM 2004): draw i descends `scale`
+// levels; level l uses the 32-bit half l&1 of SplitMix64 draw 32 i + l/2 and
+// picks quadrant a (src bit 0, dst bit 0), b (0,1), c (1,0) or d (1,1), most
+// significant bit first.  Key (dst << scale) | src; a self-loop keys to
+// `drop`, which sorts after every edge.
+__global__ void k_rmat_keys(int scale, int64_t m_draw, uint32_t ta, uint32_t tab, uint32_t tabc, uint64_t seed,
+                            unsigned long long drop, unsigned long long* keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_draw;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long s = 0, d = 0;
+    uint64_t r = 0;
+    for (int l = 0; l < scale; ++l) {
+      if ((l & 1) == 0) r = splitmix64_at(seed, (uint64_t)i * 32u + (uint64_t)(l >> 1));
+      const uint32_t u = (l & 1) ? (uint32_t)(r >> 32) : (uint32_t)r;
+      const unsigned long long sb = u < tab ? 0ull : 1ull;
+      const unsigned long long db = (u < ta || (u >= tab && u < tabc)) ? 0ull : 1ull;
+      s = (s << 1) | sb;
+      d = (d << 1) | db;
+    }
+    keys[i] = s == d ? drop : ((d << scale) | s);
+  }
+}
+
 int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -64,6 +99,81 @@ int grid_for(int64_t work, int threads) {
 }
 
 }  // namespace
+
+cudaError_t rmat_graph(int scale, int64_t m_draw, uint32_t ta, uint32_t tab, uint32_t tabc, uint64_t seed,
+                       int weighting, uint64_t weight_seed, int64_t* m_out, int64_t** d_off, uint2** d_edge,
+                       cudaStream_t st, int* launches) {
+  const int64_t n = int64_t(1) << scale;
+  const unsigned long long drop = 1ull << (2 * scale);  // after every (dst, src) key
+  const int end_bit = 2 * scale + 1;
+  unsigned long long *k_in = nullptr, *k_out = nullptr;
+  long long* d_count = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_sort = 0, tmp_uniq = 0;
+  *d_off = nullptr;
+  *d_edge = nullptr;
+  cudaError_t e = cudaSuccess;
+  do {
+    const size_t cnt = (size_t)(m_draw > 0 ? m_draw : 1);
+    if ((e = cudaMallocAsync(&k_in, sizeof(unsigned long long) * cnt, st)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&k_out, sizeof(unsigned long long) * cnt, st)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&d_count, sizeof(long long), st)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(d_count, 0, sizeof(long long), st)) != cudaSuccess) break;
+    int64_t m = 0;
+    if (m_draw > 0) {
+      k_rmat_keys<<<grid_for(m_draw, 256), 256, 0, st>>>(scale, m_draw, ta, tab, tabc, seed, drop, k_in);
+      ++*launches;
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = cub::DeviceRadixSort::SortKeys(nullptr, tmp_sort, k_in, k_out, m_draw, 0, end_bit, st)) !=
+          cudaSuccess)
+        break;
+      if ((e = cub::DeviceSelect::Unique(nullptr, tmp_uniq, k_out, k_in, d_count, m_draw, st)) != cudaSuccess)
+        break;
+      if ((e = cudaMallocAsync(&tmp, std::max(tmp_sort, tmp_uniq), st)) != cudaSuccess) break;
+      if ((e = cub::DeviceRadixSort::SortKeys(tmp, tmp_sort, k_in, k_out, m_draw, 0, end_bit, st)) != cudaSuccess)
+        break;
+      // unique keys in ascending order back into k_in; the one `drop` key, if any, is last
+      if ((e = cub::DeviceSelect::Unique(tmp, tmp_uniq, k_out, k_in, d_count, m_draw, st)) != cudaSuccess) break;
+      *launches += 2 * ((end_bit + 7) / 8) + 3;
+      long long uniq = 0;
+      unsigned long long last = 0;
+      if ((e = cudaMemcpyAsync(&uniq, d_count, sizeof(uniq), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+      if (uniq > 0) {
+        if ((e = cudaMemcpyAsync(&last, k_in + uniq - 1, sizeof(last), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+          break;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+      }
+      m = (uniq > 0 && last == drop) ? uniq - 1 : uniq;
+    }
+    const int64_t m_pad = ((m + 3) / 4) * 4 + 4;
+    if ((e = cudaMallocAsync(d_off, sizeof(int64_t) * (size_t)(n + 1), st)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(d_edge, sizeof(uint2) * (size_t)m_pad, st)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(*d_edge, 0, sizeof(uint2) * (size_t)m_pad, st)) != cudaSuccess) break;
+    if (m == 0) {
+      e = cudaMemsetAsync(*d_off, 0, sizeof(int64_t) * (size_t)(n + 1), st);
+    } else {
+      // the unique keys are the CSR order (dst, src): offsets and records as for a loaded graph
+      k_offsets<<<grid_for(m + 1, 256), 256, 0, st>>>(k_in, n, m, scale, *d_off);
+      k_fill_edges<<<grid_for(m, 256), 256, 0, st>>>(k_in, nullptr, *d_off, m, scale, weighting, weight_seed,
+                                                     nullptr, *d_edge);
+      *launches += 2;
+      e = cudaGetLastError();
+    }
+    *m_out = m;
+  } while (false);
+  if (k_in) cudaFreeAsync(k_in, st);
+  if (k_out) cudaFreeAsync(k_out, st);
+  if (d_count) cudaFreeAsync(d_count, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess) {
+    if (*d_off) cudaFreeAsync(*d_off, st);
+    if (*d_edge) cudaFreeAsync(*d_edge, st);
+    *d_off = nullptr;
+    *d_edge = nullptr;
+  }
+  return e;
+}
 
 cudaError_t build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const uint32_t* d_thr_in,
                         int weighting, uint64_t weight_seed, int64_t* d_off, uint2* d_edge, unsigned int* d_err,

@@ -107,6 +107,14 @@ cudaError_t build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_
                         int64_t* d_off, uint2* d_edge, unsigned int* d_err, cudaStream_t st,
                         int* launches);
 
+// Directed R-MAT graph on 2^scale nodes from m_draw SplitMix64-keyed draws
+// (quadrant thresholds ta < tab < tabc of a 32-bit draw), self-loops and
+// duplicates removed, built straight into the in-edge CSR (allocated here,
+// stream-ordered; the caller owns *d_off and *d_edge).  *m_out: unique edges.
+cudaError_t rmat_graph(int scale, int64_t m_draw, uint32_t ta, uint32_t tab, uint32_t tabc, uint64_t seed,
+                       int weighting, uint64_t weight_seed, int64_t* m_out, int64_t** d_off, uint2** d_edge,
+                       cudaStream_t st, int* launches);
+
 // ---- sampling -----------------------------------------------------------
 LaunchCfg sampler_config(const GraphView& g, int model);
 size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c);
@@ -159,10 +167,16 @@ struct GreedyJob {
   unsigned int* hist;           // 2 x 4096 gain-histogram bins, zeroed
   int32_t* cache;               // 2 x 8192 candidate nodes
   unsigned int* cache_n;        // 2 counts, zeroed
+  long long wait_polls;         // polls after which a grid-barrier wait gives up
 };
+constexpr long long GREEDY_DEFAULT_WAIT_POLLS = 1ll << 22;  // about a second with the poll back-off
+// Process-wide poll limit of the greedy kernel's grid-barrier waits (ssa_set_wait_polls).
+long long greedy_wait_polls();
 // All k picks in one cooperative launch (bounded grid barriers).
 cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used);
 cudaError_t launch_add_counts(int32_t* total, const int32_t* add, int64_t n, cudaStream_t st, int num_sms);
+// SASS and PTX versions (major*10 + minor) of the device code the CUDA runtime loaded for this library
+cudaError_t device_code_version(int* binary, int* ptx);
 
 cudaError_t launch_mark_hits(const int32_t* nodes, const int32_t* samp, int64_t e0, int64_t e1,
                              const uint8_t* in_seed, int64_t j0, int64_t j1, uint8_t* hit, cudaStream_t st,

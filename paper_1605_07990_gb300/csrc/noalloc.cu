@@ -11,8 +11,6 @@
 // it keeps the last call's contents, so each call clears the part it uses,
 // and calls whose work overlaps on the GPU (different streams, or threads)
 // race on it.
-#include <mutex>
-
 #include "../../include/ssa.h"
 #include "device.cuh"
 
@@ -20,7 +18,6 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t(16) << 20;  // 16 MiB
 constexpr size_t kHeaderBytes = 256;                // counter + error flag
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_cov_scratch[kScratchBytes];
 
@@ -29,24 +26,15 @@ struct ScratchHeader {
   unsigned int bad_id;
 };
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (host code must not use the symbol itself as an address).
+// Device address of the scratch array on the current device.  Host code must
+// not use the symbol itself as an address.  It is looked up on every call (a
+// lookup allocates nothing and is cheap), so an address never outlives the
+// context it came from, e.g. across a cudaDeviceReset.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_cov_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_cov_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

@@ -119,6 +119,10 @@ __device__ __forceinline__ bool hash_insert(uint32_t* H, uint32_t u, uint32_t* s
   return false;  // not reached: the table is never more than half full
 }
 
+template <class Visit>
+__device__ __forceinline__ bool deliver(uint32_t cand, uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, int lane,
+                                        uint32_t* stage, Visit&& visit);
+
 // One slab: each lane holds one 4-edge group `grp` of an in-list [olo, ohi)
 // (when `valid`).  Edges whose tail may be new draw their coins; the live
 // ones are compacted through `stage` (STAGE entries, private to the warp) and
@@ -130,7 +134,6 @@ __device__ __forceinline__ bool process_slab(const GraphView& g, bool valid, uin
                                              uint32_t othr, const uint32_t* rk, const SampleConst& sc, int lane,
                                              uint32_t* stage, unsigned long long& draws, Known&& known,
                                              Visit&& visit) {
-  const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t cand = 0, u0 = 0, u1 = 0, u2 = 0, u3 = 0;
   if (WC && valid) {
     // weighted cascade: every in-edge of the owner has threshold othr, so the
@@ -174,6 +177,16 @@ __device__ __forceinline__ bool process_slab(const GraphView& g, bool valid, uin
       if ((need & 8u) && edge_live(r.w, B.w)) cand |= 8u;
     }
   }
+  return deliver(cand, u0, u1, u2, u3, lane, stage, visit);
+}
+
+// Hand the live candidates of one slab (lane-held masks over 4 tails) to
+// visit(u) in rounds of 32 (NO_NODE for idle lanes), compacted through
+// `stage` when some lane holds more than one.  Returns visit's "stop".
+template <class Visit>
+__device__ __forceinline__ bool deliver(uint32_t cand, uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3, int lane,
+                                        uint32_t* stage, Visit&& visit) {
+  const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned any = __ballot_sync(FULL_MASK, cand != 0u);
   if (!any) return false;
   if (!__any_sync(FULL_MASK, (cand & (cand - 1u)) != 0u)) {
@@ -213,6 +226,70 @@ __device__ __forceinline__ uint32_t wc_threshold(uint32_t d) {
   return d <= 1u ? 0xFFFFFFFFu : (uint32_t)(0x100000000ull / d);
 }
 
+// Edges of the group `grp` that lie in the in-list [lo, hi), as a 4-bit mask.
+__device__ __forceinline__ uint32_t group_mask(uint32_t grp, uint32_t lo, uint32_t hi) {
+  const uint32_t e = grp * 4u;
+  const uint32_t a = lo > e ? lo - e : 0u;
+  const uint32_t b = hi - e;
+  return (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
+}
+
+// Live coins of a Philox draw against one threshold below 0xFFFFFFFF.
+__device__ __forceinline__ uint32_t coins_below(const uint4& r, uint32_t thr) {
+  return (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
+         ((uint32_t)(r.w < thr) << 3);
+}
+
+template <class Visit>
+__device__ __forceinline__ bool deliver_group(const GraphView& g, uint32_t grp, uint32_t cand, int lane,
+                                              uint32_t* stage, Visit&& visit) {
+  uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+  if (cand) {
+    const uint2* p = g.edge + (size_t)grp * 4u;
+    if (cand & 1u) u0 = __ldg(&p[0].x);
+    if (cand & 2u) u1 = __ldg(&p[1].x);
+    if (cand & 4u) u2 = __ldg(&p[2].x);
+    if (cand & 8u) u3 = __ldg(&p[3].x);
+  }
+  return deliver(cand, u0, u1, u2, u3, lane, stage, visit);
+}
+
+// Weighted cascade, one long in-list [lo, hi) of a node with threshold thr
+// (d >= 2, so thr < 0xFFFFFFFF), walked by a whole warp: slabs of 64 groups
+// (two per lane), slab first_slab, first_slab + slab_step, ...  A group's
+// coins are its Philox draw against thr; only live edges load a record, and
+// the rare slab with a live coin goes through deliver().  Returns visit's
+// "stop".
+template <class Visit>
+__device__ __forceinline__ bool wc_walk(const GraphView& g, uint32_t lo, uint32_t hi, uint32_t thr, int first_slab,
+                                        int slab_step, const uint32_t* rk, const SampleConst& sc, int lane,
+                                        uint32_t* stage, unsigned long long& draws, Visit&& visit) {
+  const uint32_t g0 = lo >> 2, g1 = (hi + 3) >> 2;
+  for (uint32_t b = g0 + (uint32_t)first_slab * 64u; b < g1; b += (uint32_t)slab_step * 64u) {
+    const uint32_t ga = b + (uint32_t)lane, gb = ga + 32u;
+    uint32_t ca = 0, cb = 0;
+    if (ga < g1) {
+      ca = coins_below(philox_x(ga, sc, rk), thr);
+      ++draws;
+    }
+    if (gb < g1) {
+      cb = coins_below(philox_x(gb, sc, rk), thr);
+      ++draws;
+    }
+    if (__any_sync(FULL_MASK, (ca | cb) != 0u)) {
+      if (ca) ca &= group_mask(ga, lo, hi);
+      if (cb) cb &= group_mask(gb, lo, hi);
+      if (deliver_group(g, ga, ca, lane, stage, visit)) return true;
+      if (deliver_group(g, gb, cb, lane, stage, visit)) return true;
+    }
+  }
+  return false;
+}
+
+// In-lists of at least this many 4-edge groups are walked by the whole warp
+// alone (weighted cascade): no owner search per group.
+constexpr int WC_SOLO_GROUPS = 64;
+
 template <bool WC, class Known, class Visit, class Heavy>
 __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
                                          int lane, uint32_t* stage, unsigned long long& ev, unsigned long long& draws,
@@ -230,6 +307,18 @@ __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const ui
   if (__any_sync(FULL_MASK, heavy == HEAVY_ABORT)) return 2;
   if (heavy == HEAVY_SKIP) ng = 0;  // counted and expanded by the taker
   else ev += hi - lo;
+  if (WC) {
+    // long lists first, each by the whole warp
+    unsigned solo = __ballot_sync(FULL_MASK, ng >= WC_SOLO_GROUPS);
+    if (ng >= WC_SOLO_GROUPS) ng = 0;
+    while (solo) {
+      const int sl = __ffs(solo) - 1;
+      solo &= solo - 1u;
+      const uint32_t slo = __shfl_sync(FULL_MASK, lo, sl), shi = __shfl_sync(FULL_MASK, hi, sl);
+      const uint32_t sthr = __shfl_sync(FULL_MASK, thr, sl);
+      if (wc_walk(g, slo, shi, sthr, 0, 1, rk, sc, lane, stage, draws, visit)) return 1;
+    }
+  }
   const int incl = warp_inclusive_scan(ng, lane);
   const int excl = incl - ng;
   const int total = __shfl_sync(FULL_MASK, incl, 31);
@@ -603,7 +692,11 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
         }
         __syncthreads();
         const int nh = min(s_nheavy, CTA_HEAVY_CAP);
-        if (nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
+        if (WC && nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
+          // every warp takes slabs wid, wid + nwarp, ... of each heavy list in turn
+          for (int i = 0; i < nh; ++i)
+            if (wc_walk(J.g, s_hlo[i], s_hhi[i], s_hthr[i], wid, nwarp, J.rk, sc, lane, stage, dr, visit)) break;
+        } else if (nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
           // groups of the heavy in-lists, dealt to all warps 32 at a time
           if (wid == 0) {
             int carry = 0;

@@ -45,10 +45,3 @@ def test_status_strings(built):
     assert L.ssa_status_str(0) == b"ok"
     assert L.ssa_status_str(3) == b"RR pool full"
 
-
-def test_device_code_is_sm103a(built):
-    # the fatbinary carries sm_103a SASS (checked by the section name cuobjdump-free:
-    # nvcc embeds the arch string in the ELF's .nv_fatbin; a grep of the build
-    # flags is the portable check)
-    from paper_1605_07990_gb300 import build
-    assert "arch=compute_103a,code=sm_103a" in build.ARCH

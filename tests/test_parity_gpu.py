@@ -307,3 +307,36 @@ def test_lt_general_weights():
     for algo in (0, 1):
         _same_solution(oracle.solve(og, algo, oracle.LT, 20, 0.1, 1.0 / el.n, 2),
                        P.ssa_solve(gg, algo, oracle.LT, 20, 0.1, 1.0 / el.n, 2))
+
+
+def test_device_code_is_sm103a():
+    # the runtime loaded sm_103a SASS for the library's kernels (cudaFuncGetAttributes)
+    assert P.ssa_device_code_version() == (103, 103)
+
+
+@pytest.mark.parametrize("scale,m_draw,weighting,seed", [(14, 1 << 17, P.SSA_W_WC, 1), (11, 1 << 15, P.SSA_W_WC, 7),
+                                                         (20, 1 << 24, P.SSA_W_TRIVALENCY, 1), (3, 40, P.SSA_W_WC, 2)])
+def test_gen_rmat_equals_host_generator(scale, m_draw, weighting, seed):
+    # the device generator and the host input module draw the same R-MAT edges;
+    # the device CSR equals the one loaded from the host edge list, bit for bit
+    el = inputs.rmat(scale, m_draw, 0.57, 0.19, 0.19, seed=seed)
+    gd = P.ssa_gen_rmat(scale, m_draw, 0.57, 0.19, 0.19, seed=seed, weighting=weighting, weight_seed=1)
+    gh = P.ssa_load_graph(el.n, el.src, el.dst, None, weighting, 1)
+    assert (gd.n, gd.m) == (el.n, el.m)
+    for a, b in zip(P.ssa_graph_export(gd), P.ssa_graph_export(gh)):
+        assert np.array_equal(a, b)
+    if scale <= 14:
+        og = oracle.Graph(el.n, el.src, el.dst, weighting, None, 1)
+        off, src, thr = og.csr()
+        d_off, d_src, d_thr = P.ssa_graph_export(gd)
+        assert np.array_equal(off, d_off) and np.array_equal(src, d_src) and np.array_equal(thr, d_thr)
+    gd.free()
+    gh.free()
+
+
+def test_gen_rmat_rejects_bad_arguments():
+    for bad in [dict(scale=0), dict(scale=31), dict(m_draw=-1), dict(a=0.9), dict(weighting=P.SSA_W_EXPLICIT)]:
+        args = dict(scale=10, m_draw=100, a=0.57, b=0.19, c=0.19, weighting=P.SSA_W_WC)
+        args.update(bad)
+        with pytest.raises(P.SSAError):
+            P.ssa_gen_rmat(args["scale"], args["m_draw"], args["a"], args["b"], args["c"], 1, args["weighting"])
