@@ -254,16 +254,31 @@ def summarise(P, name, results, ms, sm_count, clock_mhz):
     }
 
 
-def cpu_baseline(el, weighting, model, k, seed, budget_s):
+class OracleGraph(threading.Thread):
+    """The oracle's CSR of the workload, built on a host thread (the C call
+    releases the GIL) while the GPU steps run."""
+
+    def __init__(self, el, weighting):
+        super().__init__(daemon=True)
+        self.el, self.weighting, self.g, self.seconds, self.error = el, weighting, None, 0.0, None
+
+    def run(self):
+        try:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            self.g = oracle.Graph(self.el.n, self.el.src, self.el.dst, self.weighting, None, 1)
+            self.seconds = time.perf_counter() - t0
+        except Exception as e:  # reported in the bench line
+            self.error = repr(e)
+
+
+def cpu_baseline(og, t_graph, el, model, k, seed, budget_s):
     """The oracle as it stands on the host cores: the sampling phase of the step-0
     solve's stream on one thread for about budget_s, the same number of sets per
     thread over all cores (by sample range), then Max-Coverage (Algorithm 2) and
     the stare count (Eq. 1) over the one-thread sample."""
     import oracle
-    oracle.build()
-    t0 = time.perf_counter()
-    og = oracle.Graph(el.n, el.src, el.dst, weighting, None, 1)
-    t_graph = time.perf_counter() - t0
     pool = oracle.Pool(og, model, seed, 0)
     t0 = time.perf_counter()
     count, chunk = 0, 4
@@ -344,18 +359,29 @@ def serving_queries(nq, graphs_n, seed=7):
 
 
 def run_serving(args):
-    """Poisson stream of mixed queries against two resident graphs: the serving
-    loop (continuous admission, concurrent slots) against sequential solves."""
+    """The serving mix alone (bench.py --serving), as one JSON line."""
     import torch
     import __graft_entry__
-    import inputs
     __graft_entry__.build()
     import paper_1605_07990_gb300 as P
     torch.cuda.set_device(0)
+    line = serving(P, args.queries, args.slots)
+    line.update({"metric": "serving queries/s and p50/p99 latency", "unit": "queries/s",
+                 "value": line["server"]["queries_per_s"], "higher_is_better": True, "n_gpus": 1,
+                 "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serving(P, nq, slots):
+    """Poisson stream of mixed queries against two resident graphs: the serving
+    loop (continuous admission, concurrent slots, CUDA-graph rounds) against
+    sequential solves through the same library."""
+    import inputs
     els = [inputs.rmat(20, 1 << 24, seed=1), inputs.rmat(23, 1 << 27, seed=1)]
     gs = [P.ssa_load_graph(e.n, e.src, e.dst, None, P.SSA_W_WC) for e in els]
     ws = [inputs.zipf_benefit(e.n, 1.2, seed=100 + i) for i, e in enumerate(els)]
-    qs = serving_queries(args.queries, [e.n for e in els])
+    qs = serving_queries(nq, [e.n for e in els])
 
     def solve_seq(algo):
         solvers = [P.Solver(g) for g in gs]
@@ -388,7 +414,7 @@ def run_serving(args):
         return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                 "queries_per_s": len(qs) / fin, "saturated_queries_per_s": len(qs) / float(svc.sum())}
 
-    srv = P.Server(gs, slots=args.slots)
+    srv = P.Server(gs, slots=slots)
     t0 = time.perf_counter()
     tickets = []
     for q, a in zip(qs, arr):
@@ -409,20 +435,17 @@ def run_serving(args):
     sat = [srv.wait(t) for t in tk]
     t_sat = time.perf_counter() - t1
     srv.close()
-    line = {"metric": "serving queries/s and p50/p99 latency", "unit": "queries/s",
-            "value": len(qs) / t_live, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "c5 Poisson mix: R-MAT 2^20/2^24 and 2^23/2^27 (WC weights), IC/LT, "
+    line = {"config": {"workload": "Poisson mix: R-MAT 2^20/2^24 and 2^23/2^27 (WC weights), IC/LT, "
                                    "k in {1,10,100,1000}, eps in {0.05,0.1,0.2}, half targeted (Zipf 1.2)",
-                       "queries": len(qs), "arrival_rate_per_s": rate, "slots": args.slots},
+                       "queries": len(qs), "arrival_rate_per_s": rate, "slots": slots},
             "server": {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                        "queries_per_s": len(qs) / t_live, "saturated_queries_per_s": len(qs) / t_sat,
                        "answers_equal_to_sequential": same, "saturated_answers": len(sat)},
             "sequential_dssa": fifo(svc_d), "sequential_plain_ssa": fifo(svc_s),
             "mean_service_ms": {"dssa": 1e3 * float(svc_d.mean()), "ssa": 1e3 * float(svc_s.mean())}}
-    print(json.dumps(line), flush=True)
     for g in gs:
         g.free()
-    return 0
+    return line
 
 
 def main():
@@ -442,7 +465,9 @@ def main():
     ap.add_argument("--then-greedy", type=int, default=0,
                     help="with --sample-only: also index the pool and run greedy Max-Coverage for this k")
     ap.add_argument("--serving", action="store_true", help="the Poisson serving mix instead of the solve bench")
-    ap.add_argument("--queries", type=int, default=2000)
+    ap.add_argument("--queries", type=int, default=2000, help="queries of --serving")
+    ap.add_argument("--serving-queries", type=int, default=120,
+                    help="queries of the serving mix measured after the solve bench (0: skip)")
     ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -469,6 +494,10 @@ def main():
     el, weighting, algo, model, k, eps = make_graph_inputs(name)
     delta = 1.0 / el.n
     g = P.ssa_load_graph(el.n, el.src, el.dst, None, weighting, 1)
+    og_thread = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.sample_only:
+        og_thread = OracleGraph(el, weighting)
+        og_thread.start()
     if args.sample_only:
         pool = P.Pool(g, model, seed=1, stream=0).grow(args.sample_only)
         torch.cuda.synchronize()
@@ -525,6 +554,8 @@ def main():
     line["clocks"] = clocks
     line["roofline"] = summ["roofline"]
 
+    if og_thread is not None:
+        og_thread.join()  # host memory traffic of the oracle's build stays out of the e2e leg
     # end to end through the C ABI: pinned host edges -> graph upload + device CSR build -> solve -> seeds to host
     src_h = torch.from_numpy(el.src).pin_memory()
     dst_h = torch.from_numpy(el.dst).pin_memory()
@@ -564,8 +595,14 @@ def main():
         solver3.free()
         g3.free()
 
-    if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(el, weighting, model, k, seed_of(0), args.cpu_seconds)
+    if args.serving_queries > 0 and world == 1:
+        line["serving"] = serving(P, args.serving_queries, args.slots)
+    if og_thread is not None:
+        if og_thread.g is None:
+            line["cpu_baseline"] = {"unavailable": f"oracle graph build failed: {og_thread.error}"}
+        else:
+            line["cpu_baseline"] = cpu_baseline(og_thread.g, og_thread.seconds, el, model, k, seed_of(0),
+                                                args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.free()

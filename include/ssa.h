@@ -144,6 +144,12 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
 ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_samples, int32_t* mid_cap,
                         double* pilot_ms);
 ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap, int32_t heavy_groups);
+/* Queue capacity of the CTA tier's first stage when the n-bit visited bitmap
+ * lives in global memory (n/8 above 192 KB): 256-thread CTAs keep sets of up to
+ * small_queue nodes, and full-size CTAs redo larger sets.  0 restores the
+ * default min(n, 2^20).  Applies to sampler scratch created afterwards (new
+ * pools and solvers); results never depend on it.  SSA_E_ARG if negative. */
+ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue);
 
 /* Process-wide bound on the polls of each device-side wait: the grid barriers
  * of the greedy kernel (ssa_max_coverage and every solve).  A wait that reaches
@@ -229,12 +235,22 @@ typedef struct {
  * SSA_E_NOMEM, SSA_E_POOL_FULL, SSA_E_CUDA, SSA_E_TIMEOUT. */
 ssa_status ssa_solve(const ssa_graph* g, const ssa_params* p, ssa_result* out);
 
-/* A solver keeps device workspaces (RR pool, index, scratch) and a CUDA stream
- * across solves on one graph.  stream: a cudaStream_t to run on, or NULL for a
+/* A solver keeps device workspaces (sampler scratch per model, index and
+ * greedy buffers) and a CUDA stream across solves on one graph; each solve's
+ * RR pool and index return to the device's memory pool when it ends.  stream: a cudaStream_t to run on, or NULL for a
  * library-created one.  pool_bytes_cap: cap for the RR pool (0 = 60% of the
  * device memory free at creation). */
 ssa_status ssa_solver_create(const ssa_graph* g, void* stream, int64_t pool_bytes_cap, ssa_solver** out);
 ssa_status ssa_solver_solve(ssa_solver* s, const ssa_params* p, ssa_result* out);
+/* Run each round's device work after sampling -- the index of the new sets,
+ * Max-Coverage and, for D-SSA, the hit-tested stare count over R^c_t
+ * (Algorithms 2 and 4) -- as one CUDA graph instead of separate launches and
+ * host waits (on = 1; 0 = separate launches, the default).  The graph of
+ * round t is captured on the solver's stream and patched into the executable
+ * the solver keeps for round t, so later solves with the same shape reuse it.
+ * Results do not depend on this setting.  Solves that time kernel classes
+ * (ssa_result.want_kstats) launch separately. */
+ssa_status ssa_solver_set_graphs(ssa_solver* s, int32_t on);
 ssa_status ssa_solver_free(ssa_solver* s);
 
 /* ------------------------------------------------------------------------ */

@@ -77,10 +77,12 @@ EXPORTS = {
     "ssa_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "ssa_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "ssa_set_wait_polls": (C.c_int, [C.c_int64]),
+    "ssa_set_queue_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "ssa_solver_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_free": (C.c_int, [C.c_void_p]),
+    "ssa_solver_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_pool_create": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_void_p,
                                   C.POINTER(C.c_void_p)]),
     "ssa_pool_free": (C.c_int, [C.c_void_p]),
@@ -216,6 +218,10 @@ def ssa_set_tuning(g: Graph, mid_cap, heavy_groups=0x7FFFFFFF):
     _check(lib().ssa_set_tuning(g.h, int(mid_cap), int(heavy_groups)))
 
 
+def ssa_set_queue_tuning(g: Graph, small_queue=0):
+    _check(lib().ssa_set_queue_tuning(g.h, int(small_queue)))
+
+
 def ssa_set_wait_polls(polls=0):
     """Bound the polls of every device-side wait (0 = the default, about a second)."""
     _check(lib().ssa_set_wait_polls(int(polls)))
@@ -300,6 +306,11 @@ class Solver:
         r, seeds, tr = _result(k, trace_cap, want_kstats)
         _check(lib().ssa_solver_solve(self.h, C.byref(p), C.byref(r)))
         return _unpack(r, seeds, tr)
+
+    def set_graphs(self, on=True):
+        """Run each round's index, greedy and stare as one CUDA graph."""
+        _check(lib().ssa_solver_set_graphs(self.h, int(bool(on))))
+        return self
 
     def free(self):
         if self.h:

@@ -109,6 +109,7 @@ struct ssa_graph {
   mutable std::mutex tune_mu;
   mutable int tuned_mid_cap = -1;
   mutable int tuned_heavy = 0x7FFFFFFF;
+  mutable int tuned_small_qcap = 0;  // queue of the small CTAs (0: min(n, 2^20))
   GraphView view() const {
     GraphView v;
     v.n = n;
@@ -291,10 +292,11 @@ struct Sampler {
   }
 
   ssa_status init(const ssa_graph* G, int mdl, const uint32_t* benefit, Exec& X) {
-    g = G->view();
-    model = mdl;
-    lt_cumulative = (mdl == 1 && G->weighting == SSA_W_EXPLICIT) ? 1 : 0;
-    wc_implicit = G->weighting == SSA_W_WC ? 1 : 0;
+    TRY(init_scratch(G, mdl, X));
+    return begin_solve(G, benefit, X);
+  }
+  // Per-solve state on kept scratch: tuning, WRIS prefix sums, statistics.
+  ssa_status begin_solve(const ssa_graph* G, const uint32_t* benefit, Exec& X) {
     {
       std::lock_guard<std::mutex> lock(G->tune_mu);
       if (G->tuned_mid_cap >= 0) {
@@ -302,16 +304,53 @@ struct Sampler {
         heavy_groups = G->tuned_heavy;
       }
     }
-    cfg = sampler_config(g, mdl);
+    X.num_sms = cfg.num_sms;
+    edge_visits = node_visits = samples = hit_samples = 0;
+    cta_edge_visits = cta_node_visits = cta_samples = cta_store_nodes = cta_store_sets = 0;
+    draws = cta_draws = 0;
+    dev_free(bprefix, X.st);
+    wsum = 0;
+    if (benefit) {
+      std::vector<uint64_t> pre((size_t)g.n + 1, 0);
+      for (int64_t v = 0; v < g.n; ++v) pre[(size_t)v + 1] = pre[(size_t)v] + benefit[v];
+      wsum = pre[(size_t)g.n];
+      if (wsum == 0) return fail(SSA_E_ARG, "benefit weights sum to zero");
+      TRY(dev_alloc(&bprefix, (size_t)g.n + 1, X.st));
+      CU(cudaMemcpyAsync(bprefix, pre.data(), sizeof(uint64_t) * pre.size(), cudaMemcpyHostToDevice, X.st));
+      CU(cudaStreamSynchronize(X.st));
+    }
+    return SSA_OK;
+  }
+  // Scratch of the sampler tiers for one graph and model.  The kernels clear
+  // every visited bit and hash slot they set, so the scratch stays ready for
+  // the next batch and the next solve.
+  ssa_status init_scratch(const ssa_graph* G, int mdl, Exec& X) {
+    g = G->view();
+    model = mdl;
+    lt_cumulative = (mdl == 1 && G->weighting == SSA_W_EXPLICIT) ? 1 : 0;
+    wc_implicit = G->weighting == SSA_W_WC ? 1 : 0;
+    cfg = sampler_config(g, mdl, wc_implicit != 0);
+    {
+      std::lock_guard<std::mutex> lock(G->tune_mu);
+      if (G->tuned_small_qcap > 0 && !cfg.cta_smem_bitmap)
+        cfg.small_qcap = (int)std::min<int64_t>(g.n, G->tuned_small_qcap);
+    }
     X.num_sms = cfg.num_sms;
     TRY(dev_alloc(&d_ctr, 1, X.st));
     CU(cudaMallocHost(reinterpret_cast<void**>(&h_ctr), sizeof(Counters)));
     const int64_t words = (g.n + 31) / 32;
     TRY(dev_alloc(&slot_queue, (size_t)g.n * (size_t)cfg.cta_blocks, X.st));
+    // the weighted-cascade CTA tier reads -1 as "queue slot not written yet"
+    // and restores -1 after each sample
+    if (wc_implicit && mdl == 0)
+      CU(cudaMemsetAsync(slot_queue, 0xFF, sizeof(int32_t) * (size_t)g.n * (size_t)cfg.cta_blocks, X.st));
     if (!cfg.cta_smem_bitmap) {
       TRY(dev_alloc(&slot_bitmap, (size_t)words * (size_t)cfg.cta_blocks, X.st));
       CU(cudaMemsetAsync(slot_bitmap, 0, sizeof(uint32_t) * (size_t)words * (size_t)cfg.cta_blocks, X.st));
       TRY(dev_alloc(&small_queue, (size_t)cfg.small_qcap * (size_t)cfg.small_blocks, X.st));
+      if (wc_implicit && mdl == 0)
+        CU(cudaMemsetAsync(small_queue, 0xFF, sizeof(int32_t) * (size_t)cfg.small_qcap * (size_t)cfg.small_blocks,
+                           X.st));
       TRY(dev_alloc(&small_bitmap, (size_t)words * (size_t)cfg.small_blocks, X.st));
       CU(cudaMemsetAsync(small_bitmap, 0, sizeof(uint32_t) * (size_t)words * (size_t)cfg.small_blocks, X.st));
     }
@@ -322,15 +361,6 @@ struct Sampler {
       CU(cudaMemsetAsync(mid_hash, 0, sizeof(uint32_t) * warps * mid_hash_per_warp(), X.st));
       TRY(dev_alloc(&mid_queue, warps * mid_queue_per_warp(), X.st));
       TRY(dev_alloc(&mid_slots, warps * mid_queue_per_warp(), X.st));
-    }
-    if (benefit) {
-      std::vector<uint64_t> pre((size_t)g.n + 1, 0);
-      for (int64_t v = 0; v < g.n; ++v) pre[(size_t)v + 1] = pre[(size_t)v] + benefit[v];
-      wsum = pre[(size_t)g.n];
-      if (wsum == 0) return fail(SSA_E_ARG, "benefit weights sum to zero");
-      TRY(dev_alloc(&bprefix, (size_t)g.n + 1, X.st));
-      CU(cudaMemcpyAsync(bprefix, pre.data(), sizeof(uint64_t) * pre.size(), cudaMemcpyHostToDevice, X.st));
-      CU(cudaStreamSynchronize(X.st));
     }
     return SSA_OK;
   }
@@ -509,20 +539,54 @@ struct Sampler {
 
   // Hit-test batch (Estimate-Inf): hit[i] = R_{j0+i} meets the seed bits.
   ssa_status hits(uint64_t seed, uint32_t stream, int64_t j0, int64_t count, Exec& X) {
+    TRY(hits_prepare(count, X));
+    TRY(hits_issue(seed, stream, j0, count, X));
+    CU(cudaStreamSynchronize(X.st));
+    return hits_finish(count);
+  }
+  // The same batch in three parts, so that the middle one, which only queues
+  // device work (no allocation, no host wait), can be captured into a CUDA
+  // graph: buffers, then the kernels with the counters reset on the device
+  // and read back into pinned memory, then the checks and statistics.
+  ssa_status hits_prepare(int64_t count, Exec& X) {
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
     TRY(dev_grow(&big2_list, &big2_cap, count, 0, X.st));
     TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&hit, &hit_cap, count, 0, X.st));
+    return SSA_OK;
+  }
+  ssa_status hits_issue(uint64_t seed, uint32_t stream, int64_t j0, int64_t count, Exec& X) {
     SampleJob J = job(seed, stream, j0, count);
     J.mode = MODE_HIT;
     J.seed_bits = seed_bits;
     J.hit = hit;
-    TRY(run(J, X, 0));
+    CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), X.st));
+    int h = X.begin(SSA_K_SAMPLE_WARP);
+    CU(launch_sample_warp(J, cfg, X.st));
+    X.end(h);
+    h = X.begin(SSA_K_SAMPLE_CTA);
+    CU(launch_sample_cta(J, cfg, X.st));
+    X.end(h);
+    X.launches += model == 0 ? 3 : 2;
+    CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, X.st));
+    return SSA_OK;
+  }
+  ssa_status hits_finish(int64_t count) {
+    if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error");
     tally(count);
     hit_samples += count;
     return SSA_OK;
   }
 };
+
+// One cooperative greedy grid on the device at a time: a solver holds this
+// from the launch of its greedy kernel until its stream has finished it, so
+// solvers on other host threads (serving slots) never run two grids whose
+// blocks must all be resident at once.
+std::mutex& coop_mutex() {
+  static std::mutex mu;
+  return mu;
+}
 
 // Node -> set index and greedy buffers.  The pool only ever appends whole
 // batches, so the index is kept per batch: each batch is counted, scanned and
@@ -534,6 +598,8 @@ struct Cover {
     int64_t j0, j1;          // sample ids [j0, j1)
     int64_t* off = nullptr;  // n+1
     int32_t* samp = nullptr; // entries of the batch
+    int64_t e0 = 0, e1 = 0;  // its pool entries
+    bool ready = false;      // kernels queued
   };
   int64_t n = 0;
   int64_t n_pad = 0;
@@ -562,6 +628,14 @@ struct Cover {
   int64_t fr_cap = 0;
   uint8_t* hitc = nullptr;  // per-sample flags for Cov over a range
   int64_t hitc_cap = 0;
+  // pinned host copies of the greedy's results and of the stare count, so the
+  // copies back can sit inside a captured CUDA graph
+  int32_t* h_seeds = nullptr;
+  int32_t* h_gains = nullptr;
+  int h_cap = 0;
+  unsigned int* h_sync = nullptr;        // 128 words
+  unsigned long long* h_count = nullptr;
+  int64_t total_e = 0;                   // entries of the sets the next greedy covers (greedy_prepare)
 
   ssa_status init(int64_t nn, Exec& X) {
     n = nn;
@@ -579,7 +653,20 @@ struct Cover {
     TRY(dev_alloc(&cache, 2 * 8192, X.st));
     TRY(dev_alloc(&d_count, 1, X.st));
     TRY(dev_alloc(&d_first, 2, X.st));
+    CU(cudaMallocHost(reinterpret_cast<void**>(&h_sync), sizeof(unsigned int) * 128));
+    CU(cudaMallocHost(reinterpret_cast<void**>(&h_count), sizeof(unsigned long long)));
     return SSA_OK;
+  }
+  // a new solve on kept workspaces: drop the previous solve's index
+  ssa_status reset(Exec& X) {
+    drop_index(X.st);
+    CU(cudaMemsetAsync(cnt_total, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
+    return SSA_OK;
+  }
+  void drop_index(cudaStream_t st) {
+    for (auto& b : batches) free_batch(b, st);
+    batches.clear();
+    free_batch(partial_batch, st);
   }
   void free_batch(Batch& b, cudaStream_t st) {
     dev_free(b.off, st);
@@ -609,31 +696,39 @@ struct Cover {
     if (fr_tmp) cudaFreeAsync(fr_tmp, st);
     fr_tmp = nullptr;
     dev_free(hitc, st);
+    cudaStreamSynchronize(st);  // the pinned buffers may still be a copy's destination
+    if (h_seeds) cudaFreeHost(h_seeds);
+    if (h_gains) cudaFreeHost(h_gains);
+    if (h_sync) cudaFreeHost(h_sync);
+    if (h_count) cudaFreeHost(h_count);
+    h_seeds = h_gains = nullptr;
+    h_sync = nullptr;
+    h_count = nullptr;
+    h_cap = 0;
   }
 
-  // index of the samples [j0, j1) whose entries lie in [e0, e1); counts land in cnt_tmp
-  ssa_status index_range(const DevPool& P, int64_t j0, int64_t j1, int64_t e0, int64_t e1, bool filter, Batch& B,
-                         Exec& X) {
-    B.j0 = j0;
-    B.j1 = j1;
+  ssa_status index_alloc(Batch& B, Exec& X) {
     TRY(dev_alloc(&B.off, (size_t)n + 1, X.st));
-    TRY(dev_alloc(&B.samp, (size_t)std::max<int64_t>(e1 - e0, 1), X.st));
+    TRY(dev_alloc(&B.samp, (size_t)std::max<int64_t>(B.e1 - B.e0, 1), X.st));
+    return SSA_OK;
+  }
+  // index of the samples [B.j0, B.j1) whose entries lie in [B.e0, B.e1); counts land in cnt_tmp
+  ssa_status index_kernels(const DevPool& P, const Batch& B, bool filter, Exec& X) {
     CU(cudaMemsetAsync(cnt_tmp, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
-    CU(launch_count_nodes(P.nodes, filter ? P.samp : nullptr, e0, e1, j0, j1, cnt_tmp, X.st, X.num_sms));
+    CU(launch_count_nodes(P.nodes, filter ? P.samp : nullptr, B.e0, B.e1, B.j0, B.j1, cnt_tmp, X.st, X.num_sms));
     int l = 0;
     CU(launch_exclusive_scan(cnt_tmp, n, B.off, scan_tmp, X.st, &l));
     // positions inside the batch's own sample array: offsets start at 0
     CU(cudaMemcpyAsync(cur, B.off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, X.st));
-    CU(launch_scatter_index(P.nodes, P.samp, e0, e1, j0, j1, cur, B.samp, X.st, X.num_sms));
+    CU(launch_scatter_index(P.nodes, P.samp, B.e0, B.e1, B.j0, B.j1, cur, B.samp, X.st, X.num_sms));
     X.launches += 2 + l;
     return SSA_OK;
   }
 
-  // Make the index cover the sets [0, N): cached whole batches plus, for a
-  // cut inside a batch, a temporary partial one.  Leaves the counts of [0, N)
-  // in `cnt`.
-  ssa_status build_index(const DevPool& P, int64_t N, Exec& X) {
-    int h = X.begin(SSA_K_INDEX);
+  // Buffers for the index of every whole pool batch below N not indexed yet.
+  // *whole: N lies on a batch boundary, so index_issue needs no temporary
+  // partial batch (and allocates nothing).
+  ssa_status index_prepare(const DevPool& P, int64_t N, bool* whole, Exec& X) {
     free_batch(partial_batch, X.st);
     if (!batches.empty() && batches.back().j1 > N) {
       // a smaller cut than before (direct callers): start the cache over
@@ -641,7 +736,6 @@ struct Cover {
       batches.clear();
       CU(cudaMemsetAsync(cnt_total, 0, sizeof(int32_t) * (size_t)n_pad, X.st));
     }
-    // cache every whole pool batch below N that is not indexed yet
     for (size_t i = 1; i < P.bounds.size(); ++i) {
       const int64_t j0 = P.bounds[i - 1].first, j1 = P.bounds[i].first;
       if (j1 > N) break;
@@ -649,17 +743,37 @@ struct Cover {
       if (batches.size() >= (size_t)GREEDY_MAX_LISTS - 1)
         return fail(SSA_E_INTERNAL, "more than %d index batches", GREEDY_MAX_LISTS - 1);
       Batch B;
-      TRY(index_range(P, j0, j1, P.bounds[i - 1].second, P.bounds[i].second, false, B, X));
+      B.j0 = j0;
+      B.j1 = j1;
+      B.e0 = P.bounds[i - 1].second;
+      B.e1 = P.bounds[i].second;
+      TRY(index_alloc(B, X));
+      batches.push_back(B);
+    }
+    *whole = (batches.empty() ? 0 : batches.back().j1) >= N;
+    return SSA_OK;
+  }
+
+  // Queue the index kernels of the batches index_prepare added (each batch is
+  // counted, scanned and scattered once) and, for a cut inside a batch, of a
+  // temporary partial one.  Leaves the counts of [0, N) in `cnt`.
+  ssa_status index_issue(const DevPool& P, int64_t N, Exec& X) {
+    int h = X.begin(SSA_K_INDEX);
+    for (auto& B : batches) {
+      if (B.ready) continue;
+      TRY(index_kernels(P, B, false, X));
       CU(launch_add_counts(cnt_total, cnt_tmp, n, X.st, X.num_sms));
       X.launches += 1;
-      batches.push_back(B);
+      B.ready = true;
     }
     CU(cudaMemcpyAsync(cnt, cnt_total, sizeof(int32_t) * (size_t)n_pad, cudaMemcpyDeviceToDevice, X.st));
     const int64_t covered_to = batches.empty() ? 0 : batches.back().j1;
     if (covered_to < N) {
-      int64_t e0, e1;
-      P.entry_range(covered_to, N, &e0, &e1);
-      TRY(index_range(P, covered_to, N, e0, e1, true, partial_batch, X));
+      partial_batch.j0 = covered_to;
+      partial_batch.j1 = N;
+      P.entry_range(covered_to, N, &partial_batch.e0, &partial_batch.e1);
+      TRY(index_alloc(partial_batch, X));
+      TRY(index_kernels(P, partial_batch, true, X));
       CU(launch_add_counts(cnt, cnt_tmp, n, X.st, X.num_sms));
       X.launches += 1;
     }
@@ -667,11 +781,20 @@ struct Cover {
     return SSA_OK;
   }
 
-  // Max-Coverage (Algorithm 2) over sets [0, N): seeds/gains to host.
-  ssa_status greedy(const DevPool& P, int64_t N, int k, int32_t* seeds, int64_t* gains, int64_t* cov, Exec& X) {
+  // Make the index cover the sets [0, N).
+  ssa_status build_index(const DevPool& P, int64_t N, Exec& X) {
+    bool whole = false;
+    TRY(index_prepare(P, N, &whole, X));
+    return index_issue(P, N, X);
+  }
+
+  // Max-Coverage (Algorithm 2) over sets [0, N) in three parts, so that the
+  // middle one (device work only) can sit inside a captured CUDA graph:
+  // buffers, then the kernel and the copies of its results into pinned
+  // memory, then the checks once the stream has finished.
+  ssa_status greedy_prepare(const DevPool& P, int64_t N, int k, Exec& X) {
     // packed argmax keys (gain + 1) << 31 | (2^31 - 1 - v) stay below 2^62
     if (N >= INT32_MAX) return fail(SSA_E_ARG, "greedy over %lld sets: at most 2^31 - 2", (long long)N);
-    TRY(build_index(P, N, X));
     if (k > k_cap) {
       dev_free(d_seeds, X.st);
       dev_free(d_gains, X.st);
@@ -679,16 +802,27 @@ struct Cover {
       TRY(dev_alloc(&d_gains, (size_t)k, X.st));
       k_cap = k;
     }
-    TRY(dev_grow(&covered, &covered_cap, std::max<int64_t>(N, 1), 0, X.st));
-    int64_t total_e = 0;  // entries of sets [0, N), an upper bound when N cuts a batch
-    {
-      // queued decrement chunks of one pick: a set longer than 2048 entries
-      // queues ceil(len / 2048) < len / 1024 chunks
-      int64_t e0 = 0, e1 = 0;
-      P.entry_range(0, N, &e0, &e1);
-      total_e = e1 - e0;
-      TRY(dev_grow(&chunk_q, &chunk_cap, e1 / 1024 + 1, 0, X.st));
+    if (k > h_cap) {
+      CU(cudaStreamSynchronize(X.st));  // the old buffers may still be a copy's destination
+      if (h_seeds) cudaFreeHost(h_seeds);
+      if (h_gains) cudaFreeHost(h_gains);
+      h_seeds = h_gains = nullptr;
+      h_cap = 0;
+      CU(cudaMallocHost(reinterpret_cast<void**>(&h_seeds), sizeof(int32_t) * (size_t)k));
+      CU(cudaMallocHost(reinterpret_cast<void**>(&h_gains), sizeof(int32_t) * (size_t)k));
+      h_cap = k;
     }
+    TRY(dev_grow(&covered, &covered_cap, std::max<int64_t>(N, 1), 0, X.st));
+    // entries of sets [0, N), an upper bound when N cuts a batch; queued
+    // decrement chunks of one pick: a set longer than 2048 entries queues
+    // ceil(len / 2048) < len / 1024 chunks
+    int64_t e0 = 0, e1 = 0;
+    P.entry_range(0, N, &e0, &e1);
+    total_e = e1 - e0;
+    TRY(dev_grow(&chunk_q, &chunk_cap, e1 / 1024 + 1, 0, X.st));
+    return SSA_OK;
+  }
+  ssa_status greedy_issue(const DevPool& P, int64_t N, int k, Exec& X) {
     int h = X.begin(SSA_K_GREEDY);
     CU(cudaMemsetAsync(covered, 0, (size_t)std::max<int64_t>(N, 1), X.st));
     CU(cudaMemsetAsync(sync, 0, sizeof(unsigned int) * 128, X.st));
@@ -720,28 +854,36 @@ struct Cover {
     J.cache_n = hist + 2 * 4096;
     J.wait_polls = greedy_wait_polls();
     int blocks = 0;
-    // one cooperative greedy grid on the device at a time (solvers on other
-    // host threads, e.g. serving slots, wait here)
-    static std::mutex coop_mu;
-    std::lock_guard<std::mutex> coop_lock(coop_mu);
     CU(launch_greedy(J, X.st, X.num_sms, &blocks));
     X.end(h);
     X.launches += 1;
-    std::vector<int32_t> g32((size_t)k);
-    unsigned int hsync[128] = {};
-    CU(cudaMemcpyAsync(seeds, d_seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
-    CU(cudaMemcpyAsync(g32.data(), d_gains, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
-    CU(cudaMemcpyAsync(hsync, sync, sizeof(hsync), cudaMemcpyDeviceToHost, X.st));
-    CU(cudaStreamSynchronize(X.st));
-    if (hsync[64] == 2u) return fail(SSA_E_INTERNAL, "greedy decrement queue overflow");
-    if (hsync[64]) return fail(SSA_E_TIMEOUT, "greedy grid barrier timed out");
+    CU(cudaMemcpyAsync(h_seeds, d_seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
+    CU(cudaMemcpyAsync(h_gains, d_gains, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
+    CU(cudaMemcpyAsync(h_sync, sync, sizeof(unsigned int) * 128, cudaMemcpyDeviceToHost, X.st));
+    return SSA_OK;
+  }
+  ssa_status greedy_finish(int k, int32_t* seeds, int64_t* gains, int64_t* cov) {
+    if (h_sync[64] == 2u) return fail(SSA_E_INTERNAL, "greedy decrement queue overflow");
+    if (h_sync[64]) return fail(SSA_E_TIMEOUT, "greedy grid barrier timed out");
     int64_t c = 0;
     for (int i = 0; i < k; ++i) {
-      gains[i] = g32[(size_t)i];
-      c += g32[(size_t)i];
+      seeds[i] = h_seeds[i];
+      gains[i] = h_gains[i];
+      c += h_gains[i];
     }
     *cov = c;
     return SSA_OK;
+  }
+  // Max-Coverage (Algorithm 2) over sets [0, N): seeds/gains to host.
+  ssa_status greedy(const DevPool& P, int64_t N, int k, int32_t* seeds, int64_t* gains, int64_t* cov, Exec& X) {
+    TRY(greedy_prepare(P, N, k, X));
+    TRY(build_index(P, N, X));
+    {
+      std::lock_guard<std::mutex> coop_lock(coop_mutex());
+      TRY(greedy_issue(P, N, k, X));
+      CU(cudaStreamSynchronize(X.st));
+    }
+    return greedy_finish(k, seeds, gains, cov);
   }
 
   // Cov (Eq. 1) of the seeds currently flagged in in_seed over sets [a, b).
@@ -771,23 +913,33 @@ struct Cover {
 
 // Cov of the seeds over the fresh sets [j0, j0+count) of `stream`, sampled in
 // hit-test mode (each sample stops at its first seed).
-ssa_status stare_hits(Sampler& S, Cover& C, uint64_t seed, uint32_t stream, int64_t j0, int64_t count,
-                      const int32_t* d_seeds, int k, int64_t* cov, Exec& X) {
+// (split like the greedy: the issue part only queues device work)
+ssa_status stare_issue(Sampler& S, Cover& C, uint64_t seed, uint32_t stream, int64_t j0, int64_t count,
+                       const int32_t* d_seeds, int k, Exec& X) {
   const int64_t words = (S.g.n + 31) / 32;
   CU(cudaMemsetAsync(S.seed_bits, 0, sizeof(uint32_t) * (size_t)words, X.st));
   CU(launch_set_bits(d_seeds, k, S.seed_bits, nullptr, X.st));
   X.launches += 1;
-  TRY(S.hits(seed, stream, j0, count, X));
+  TRY(S.hits_issue(seed, stream, j0, count, X));
   int h = X.begin(SSA_K_STARE);
   CU(cudaMemsetAsync(C.d_count, 0, sizeof(unsigned long long), X.st));
   CU(launch_count_flags(S.hit, count, C.d_count, X.st, X.num_sms));
   X.end(h);
   X.launches += 1;
-  unsigned long long c = 0;
-  CU(cudaMemcpyAsync(&c, C.d_count, sizeof(c), cudaMemcpyDeviceToHost, X.st));
-  CU(cudaStreamSynchronize(X.st));
-  *cov = (int64_t)c;
+  CU(cudaMemcpyAsync(C.h_count, C.d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, X.st));
   return SSA_OK;
+}
+ssa_status stare_finish(Sampler& S, Cover& C, int64_t count, int64_t* cov) {
+  TRY(S.hits_finish(count));
+  *cov = (int64_t)*C.h_count;
+  return SSA_OK;
+}
+ssa_status stare_hits(Sampler& S, Cover& C, uint64_t seed, uint32_t stream, int64_t j0, int64_t count,
+                      const int32_t* d_seeds, int k, int64_t* cov, Exec& X) {
+  TRY(S.hits_prepare(count, X));
+  TRY(stare_issue(S, C, seed, stream, j0, count, d_seeds, k, X));
+  CU(cudaStreamSynchronize(X.st));
+  return stare_finish(S, C, count, cov);
 }
 
 // Estimate-Inf (Algorithm 3) on the device: hit-test batches of fresh sets
@@ -935,6 +1087,27 @@ struct ssa_solver {
   bool own_stream = false;
   Exec X;
   int64_t byte_cap = 0;
+  // workspaces kept across solves: sampler scratch per model, index and greedy buffers
+  Sampler S[2];
+  bool s_ready[2] = {false, false};
+  Cover C;
+  bool c_ready = false;
+  // CUDA graphs of a round's device work (index, greedy, stare), one
+  // executable per (algorithm, round), patched in place by later solves
+  bool use_graphs = false;
+  std::vector<cudaGraphExec_t> gexec;
+  int64_t graph_launches = 0;
+
+  void release() {
+    for (auto e : gexec)
+      if (e) cudaGraphExecDestroy(e);
+    gexec.clear();
+    for (int m = 0; m < 2; ++m)
+      if (s_ready[m]) S[m].release(X.st);
+    if (c_ready) C.release(X.st);
+    s_ready[0] = s_ready[1] = c_ready = false;
+    cudaStreamSynchronize(X.st);
+  }
 };
 
 namespace {
@@ -947,6 +1120,46 @@ ssa_status check_params(const ssa_graph* g, const ssa_params* p) {
   if (p->algo != SSA_ALGO_SSA && p->algo != SSA_ALGO_DSSA) return fail(SSA_E_ARG, "unknown algorithm");
   if (p->model == SSA_LT && g->weighting == SSA_W_TRIVALENCY)
     return fail(SSA_E_ARG, "LT needs in-weights that sum to at most 1: SSA_W_WC or SSA_W_EXPLICIT");
+  return SSA_OK;
+}
+
+// Run `issue` (device work only: kernels, memsets, copies into pinned
+// memory) as a CUDA graph on the solver's stream: captured, patched into the
+// executable cached under `slot` when the topology matches the last one
+// (cudaGraphExecUpdate), else instantiated; then launched and waited for.
+template <class F>
+ssa_status run_graph(ssa_solver* sv, size_t slot, F&& issue) {
+  Exec& X = sv->X;
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(X.st, cudaStreamCaptureModeThreadLocal));
+  const ssa_status st = issue();
+  const cudaError_t ec = cudaStreamEndCapture(X.st, &graph);
+  if (st != SSA_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ec != cudaSuccess || !graph) return fail(SSA_E_CUDA, "round capture failed: %s", cudaGetErrorString(ec));
+  if (slot >= sv->gexec.size()) sv->gexec.resize(slot + 1, nullptr);
+  cudaGraphExec_t& ex = sv->gexec[slot];
+  if (ex) {
+    cudaGraphExecUpdateResultInfo info{};
+    if (cudaGraphExecUpdate(ex, graph, &info) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (!ex) e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    ex = nullptr;
+    return fail(SSA_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  std::lock_guard<std::mutex> lock(coop_mutex());  // the graph holds a cooperative greedy launch
+  CU(cudaGraphLaunch(ex, X.st));
+  CU(cudaStreamSynchronize(X.st));
+  sv->graph_launches += 1;
   return SSA_OK;
 }
 
@@ -973,9 +1186,9 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     if (!tuned) TRY(autotune_ic(g, 4096, X, nullptr, nullptr));
     X.launches = 0;
   }
-  Sampler S;
+  Sampler& S = sv->S[p->model];
+  Cover& C = sv->C;
   DevPool pool;
-  Cover C;
   pool.byte_cap = p->pool_bytes_cap > 0 ? p->pool_bytes_cap : sv->byte_cap;
   ssa_status st = SSA_OK;
   std::vector<int32_t> seeds((size_t)k);
@@ -983,9 +1196,55 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
   int32_t t = 0;
   int64_t extra_rr = 0;
   double influence = 0.0;
+  const bool graphs = sv->use_graphs && !X.timing;
+  // Max-Coverage over the whole batches [0, N), and for D-SSA the stare count
+  // over the hit-tested check half [N, 2N): as one CUDA graph when enabled
+  auto greedy_round = [&](int64_t N, int64_t* cov, int64_t* c) -> ssa_status {
+    bool whole = false;
+    TRY(C.greedy_prepare(pool, N, k, X));
+    TRY(C.index_prepare(pool, N, &whole, X));
+    if (c) TRY(S.hits_prepare(N, X));
+    if (graphs && whole) {
+      TRY(run_graph(sv, (size_t)(dssa ? 64 : 0) + (size_t)t, [&]() -> ssa_status {
+        TRY(C.index_issue(pool, N, X));
+        TRY(C.greedy_issue(pool, N, k, X));
+        return c ? stare_issue(S, C, p->seed, 0, N, N, C.d_seeds, k, X) : SSA_OK;
+      }));
+    } else {
+      TRY(C.index_issue(pool, N, X));
+      {
+        std::lock_guard<std::mutex> lock(coop_mutex());
+        TRY(C.greedy_issue(pool, N, k, X));
+        CU(cudaStreamSynchronize(X.st));
+      }
+      if (c) {
+        TRY(stare_issue(S, C, p->seed, 0, N, N, C.d_seeds, k, X));
+        CU(cudaStreamSynchronize(X.st));
+      }
+    }
+    TRY(C.greedy_finish(k, seeds.data(), gains.data(), cov));
+    return c ? stare_finish(S, C, N, c) : SSA_OK;
+  };
   do {
-    if ((st = S.init(g, p->model, p->benefit, X)) != SSA_OK) break;
-    if ((st = C.init(n, X)) != SSA_OK) break;
+    if (!sv->s_ready[p->model]) {
+      sv->s_ready[p->model] = true;  // release() frees whatever init_scratch allocated
+      if ((st = S.init_scratch(g, p->model, X)) != SSA_OK) {
+        S.release(X.st);
+        sv->s_ready[p->model] = false;
+        break;
+      }
+    }
+    if ((st = S.begin_solve(g, p->benefit, X)) != SSA_OK) break;
+    if (!sv->c_ready) {
+      sv->c_ready = true;
+      if ((st = C.init(n, X)) != SSA_OK) {
+        C.release(X.st);
+        sv->c_ready = false;
+        break;
+      }
+    } else if ((st = C.reset(X)) != SSA_OK) {
+      break;
+    }
     const double scale = p->benefit ? (double)S.wsum : (double)n;
     const int64_t base = (int64_t)std::ceil(P.lambda);
     for (;;) {
@@ -1008,7 +1267,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
         rec.eps3 = P.eps3;
         if ((st = S.append(pool, p->seed, 0, N - pool.count, X)) != SSA_OK) break;
         int64_t cov = 0;
-        if ((st = C.greedy(pool, N, k, seeds.data(), gains.data(), &cov, X)) != SSA_OK) break;
+        if ((st = greedy_round(N, &cov, nullptr)) != SSA_OK) break;
         rec.cov = cov;
         influence = (double)cov * scale / (double)N;
         if ((double)cov >= P.lambda1) {  // condition C1
@@ -1037,8 +1296,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
         // it becomes the second half of R_{t+1} (same keys, same sets).
         if (t == 1 && (st = S.append(pool, p->seed, 0, N, X)) != SSA_OK) break;
         int64_t cov = 0, c = 0;
-        if ((st = C.greedy(pool, N, k, seeds.data(), gains.data(), &cov, X)) != SSA_OK) break;
-        if ((st = stare_hits(S, C, p->seed, 0, N, N, C.d_seeds, k, &c, X)) != SSA_OK) break;
+        if ((st = greedy_round(N, &cov, &c)) != SSA_OK) break;
         rec.cov = cov;
         rec.check_cov = c;
         influence = (double)cov * scale / (double)N;
@@ -1094,9 +1352,11 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
   } else {
     X.collect(nullptr);
   }
+  // the RR pool and this solve's index go back to the device's memory pool;
+  // the fixed-size scratch stays with the solver
   pool.release(X.st);
-  S.release(X.st);
-  C.release(X.st);
+  if (sv->c_ready) C.drop_index(X.st);
+  if (sv->s_ready[p->model]) dev_free(S.bprefix, X.st);
   cudaStreamSynchronize(X.st);
   out->seconds = now_s() - t0;
   return st;
@@ -1326,6 +1586,13 @@ ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_sampl
   return SSA_OK;
 }
 
+ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue) {
+  if (!g || small_queue < 0) return fail(SSA_E_ARG, "need a graph and small_queue >= 0");
+  std::lock_guard<std::mutex> lock(g->tune_mu);
+  g->tuned_small_qcap = small_queue;
+  return SSA_OK;
+}
+
 ssa_status ssa_set_wait_polls(int64_t polls) {
   if (polls < 0) return fail(SSA_E_ARG, "polls must be >= 0");
   g_wait_polls.store(polls == 0 ? GREEDY_DEFAULT_WAIT_POLLS : (long long)polls, std::memory_order_relaxed);
@@ -1371,9 +1638,16 @@ ssa_status ssa_solver_solve(ssa_solver* s, const ssa_params* p, ssa_result* out)
   return solve_impl(s, p, out);
 }
 
+ssa_status ssa_solver_set_graphs(ssa_solver* s, int32_t on) {
+  if (!s) return fail(SSA_E_ARG, "null solver");
+  s->use_graphs = on != 0;
+  return SSA_OK;
+}
+
 ssa_status ssa_solver_free(ssa_solver* s) {
   if (!s) return SSA_OK;
   cudaStreamSynchronize(s->X.st);
+  s->release();
   if (s->own_stream) cudaStreamDestroy(s->X.st);
   s->X.st = nullptr;
   delete s;

@@ -746,9 +746,18 @@ cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int*
   // cache slices fit in shared memory; one tally slot and one reducing thread per block
   if ((long long)blocks * HBINS < CACHE_MAX || blocks > 1024) return cudaErrorInvalidConfiguration;
   *blocks_used = blocks;
-  GreedyJob j = J;
-  void* args[] = {&j};
-  return cudaLaunchCooperativeKernel((const void*)k_greedy, dim3(blocks), dim3(1024), args, 0, st);
+  // a cooperative launch (all blocks resident at once), also valid inside a stream capture
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_greedy, J);
 }
 
 cudaError_t device_code_version(int* binary, int* ptx) {

@@ -116,7 +116,7 @@ cudaError_t rmat_graph(int scale, int64_t m_draw, uint32_t ta, uint32_t tab, uin
                        cudaStream_t st, int* launches);
 
 // ---- sampling -----------------------------------------------------------
-LaunchCfg sampler_config(const GraphView& g, int model);
+LaunchCfg sampler_config(const GraphView& g, int model, bool wc_implicit);
 size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c);
 size_t mid_tier_words(const LaunchCfg& c);  // number of warps of the global-memory tier
 int mid_tier_max_cap();

@@ -254,35 +254,55 @@ __device__ __forceinline__ bool deliver_group(const GraphView& g, uint32_t grp, 
   return deliver(cand, u0, u1, u2, u3, lane, stage, visit);
 }
 
-// Weighted cascade, one long in-list [lo, hi) of a node with threshold thr
-// (d >= 2, so thr < 0xFFFFFFFF), walked by a whole warp: slabs of 64 groups
-// (two per lane), slab first_slab, first_slab + slab_step, ...  A group's
-// coins are its Philox draw against thr; only live edges load a record, and
-// the rare slab with a live coin goes through deliver().  Returns visit's
-// "stop".
+// Weighted cascade: one slab of an in-list [lo, hi) of a node with threshold
+// thr (d >= 2, so thr < 0xFFFFFFFF): the WC_SLAB groups from group b on (up
+// to the list's last group g1 - 1), four per lane.  A group's coins are its
+// Philox draw against thr; only live edges load a record, and the rare slab
+// with a live coin goes through deliver().  A full slab runs its four draws
+// per lane unconditionally, as independent chains.  Returns visit's "stop".
+constexpr uint32_t WC_SLAB = 128;
+
 template <class Visit>
-__device__ __forceinline__ bool wc_walk(const GraphView& g, uint32_t lo, uint32_t hi, uint32_t thr, int first_slab,
-                                        int slab_step, const uint32_t* rk, const SampleConst& sc, int lane,
+__device__ __forceinline__ bool wc_slab(const GraphView& g, uint32_t lo, uint32_t hi, uint32_t thr, uint32_t b,
+                                        uint32_t g1, const uint32_t* rk, const SampleConst& sc, int lane,
                                         uint32_t* stage, unsigned long long& draws, Visit&& visit) {
-  const uint32_t g0 = lo >> 2, g1 = (hi + 3) >> 2;
-  for (uint32_t b = g0 + (uint32_t)first_slab * 64u; b < g1; b += (uint32_t)slab_step * 64u) {
-    const uint32_t ga = b + (uint32_t)lane, gb = ga + 32u;
-    uint32_t ca = 0, cb = 0;
-    if (ga < g1) {
-      ca = coins_below(philox_x(ga, sc, rk), thr);
-      ++draws;
-    }
-    if (gb < g1) {
-      cb = coins_below(philox_x(gb, sc, rk), thr);
-      ++draws;
-    }
-    if (__any_sync(FULL_MASK, (ca | cb) != 0u)) {
-      if (ca) ca &= group_mask(ga, lo, hi);
-      if (cb) cb &= group_mask(gb, lo, hi);
-      if (deliver_group(g, ga, ca, lane, stage, visit)) return true;
-      if (deliver_group(g, gb, cb, lane, stage, visit)) return true;
+  uint32_t c[4];
+  if (b + WC_SLAB <= g1) {
+    uint4 r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = philox_x(b + (uint32_t)(32 * u + lane), sc, rk);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = coins_below(r[u], thr);
+    draws += 4;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t gg = b + (uint32_t)(32 * u + lane);
+      c[u] = 0u;
+      if (gg < g1) {
+        c[u] = coins_below(philox_x(gg, sc, rk), thr);
+        ++draws;
+      }
     }
   }
+  if (!__any_sync(FULL_MASK, (c[0] | c[1] | c[2] | c[3]) != 0u)) return false;
+#pragma unroll 1
+  for (int u = 0; u < 4; ++u) {
+    const uint32_t gg = b + (uint32_t)(32 * u + lane);
+    const uint32_t cu = c[u] ? (c[u] & group_mask(gg, lo, hi)) : 0u;
+    if (deliver_group(g, gg, cu, lane, stage, visit)) return true;
+  }
+  return false;
+}
+
+// A whole in-list walked by one warp, slab after slab.
+template <class Visit>
+__device__ __forceinline__ bool wc_walk(const GraphView& g, uint32_t lo, uint32_t hi, uint32_t thr,
+                                        const uint32_t* rk, const SampleConst& sc, int lane, uint32_t* stage,
+                                        unsigned long long& draws, Visit&& visit) {
+  const uint32_t g1 = (hi + 3) >> 2;
+  for (uint32_t b = lo >> 2; b < g1; b += WC_SLAB)
+    if (wc_slab(g, lo, hi, thr, b, g1, rk, sc, lane, stage, draws, visit)) return true;
   return false;
 }
 
@@ -316,7 +336,7 @@ __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const ui
       solo &= solo - 1u;
       const uint32_t slo = __shfl_sync(FULL_MASK, lo, sl), shi = __shfl_sync(FULL_MASK, hi, sl);
       const uint32_t sthr = __shfl_sync(FULL_MASK, thr, sl);
-      if (wc_walk(g, slo, shi, sthr, 0, 1, rk, sc, lane, stage, draws, visit)) return 1;
+      if (wc_walk(g, slo, shi, sthr, rk, sc, lane, stage, draws, visit)) return 1;
     }
   }
   const int incl = warp_inclusive_scan(ng, lane);
@@ -592,7 +612,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
 //         a set that outgrows the queue goes on to KIND 2.
 // KIND 2: full-size CTAs (global bitmap, queue of n entries) for those sets.
 template <int MODE, bool SMEM_BITMAP, int KIND, bool WC>
-__global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(SampleJob J) {
+__global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, KIND == 1 ? 4 : 1) k_sample_cta(SampleJob J) {
   constexpr int WARPS = KIND == 1 ? 8 : 32;
   extern __shared__ __align__(16) uint32_t s_bits[];
   __shared__ long long s_item;
@@ -601,8 +621,11 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
   __shared__ uint32_t s_stage[WARPS][STAGE];
   // heavy in-lists of the current level, expanded by all warps together
   __shared__ uint32_t s_hlo[CTA_HEAVY_CAP], s_hhi[CTA_HEAVY_CAP], s_hthr[WC ? CTA_HEAVY_CAP : 1];
-  __shared__ int s_hpref[CTA_HEAVY_CAP];
+  __shared__ int s_hpref[CTA_HEAVY_CAP];  // weighted cascade: slab count of each split list (0: not posted)
   __shared__ int s_nheavy, s_htotal, s_hnext;
+  // weighted cascade: queue head, warps holding work, split lists and their slab cursors
+  __shared__ int s_head, s_active, s_nsplit;
+  __shared__ int s_hnext_slab[WC ? CTA_HEAVY_CAP : 1];
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
   const int64_t n = J.g.n;
   const int64_t qcap = KIND == 1 ? (int64_t)J.small_qcap : n;
@@ -662,16 +685,143 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
         if (MODE == MODE_HIT) return __any_sync(FULL_MASK, *(volatile int*)&s_hit != 0);
         return false;
       };
+      if constexpr (WC) {
+        // Weighted cascade without level barriers: any visiting order reaches
+        // the same set (the coins are keyed per edge), so the warps pull work
+        // as it appears -- up to 32 queued nodes at a time, or one slab of a
+        // long in-list that a warp posted to the split table -- and the sample
+        // ends when nothing is queued or split and no warp holds work.  A
+        // queue slot reads -1 until its node is written, so a claimed slot
+        // whose writer has reserved but not yet stored it is waited for.
+        auto take_split = [&](int32_t, uint32_t lo, uint32_t hi, int) -> int {
+          const int slot = atomicAdd(&s_nsplit, 1);
+          if (slot >= CTA_HEAVY_CAP) return 0;  // table full: this warp walks the list itself
+          s_hlo[slot] = lo;
+          s_hhi[slot] = hi;
+          s_hthr[slot] = wc_threshold(hi - lo);
+          s_hnext_slab[slot] = 0;
+          __threadfence_block();
+          *(volatile int*)&s_hpref[slot] = (int)((((hi + 3) >> 2) - (lo >> 2) + WC_SLAB - 1) / WC_SLAB);
+          ev += hi - lo;
+          return HEAVY_SKIP;
+        };
+        auto stopped = [&]() -> bool {
+          return (MODE == MODE_HIT && *(volatile int*)&s_hit) || (KIND == 1 && *(volatile int*)&s_tail > qcap);
+        };
+        if (tid == 0) {
+          s_head = 0;
+          s_active = 0;
+          s_nsplit = 0;
+        }
+        for (int i = tid; i < CTA_HEAVY_CAP; i += nthr) s_hpref[i] = 0;  // slab counts: 0 = not posted yet
+        __syncthreads();
+        const int qlim = (int)(qcap < 0x7FFFFFFF ? qcap : 0x7FFFFFFF);  // queue slots that can be written
+        int split_from = 0;  // lane 0: split slots below this are exhausted
+        long long idle = 0;
+        // Every claim and every decision is taken by lane 0 and broadcast, so
+        // the warp stays converged for the shuffles and ballots below.
+        for (;;) {
+          if (__any_sync(FULL_MASK, stopped())) break;
+          // (a) a slab of a posted long list
+          int slot = -1, sl = 0;
+          if (lane == 0) {
+            const int nsplit = min(*(volatile int*)&s_nsplit, CTA_HEAVY_CAP);
+            for (int i = split_from; i < nsplit; ++i) {
+              const int ns = *(volatile int*)&s_hpref[i];
+              if (ns == 0) continue;  // still being posted
+              if (*(volatile int*)&s_hnext_slab[i] >= ns) {
+                if (i == split_from) ++split_from;
+                continue;
+              }
+              atomicAdd(&s_active, 1);
+              const int x = atomicAdd(&s_hnext_slab[i], 1);
+              if (x < ns) {
+                slot = i;
+                sl = x;
+                break;
+              }
+              atomicSub(&s_active, 1);
+            }
+          }
+          slot = __shfl_sync(FULL_MASK, slot, 0);
+          sl = __shfl_sync(FULL_MASK, sl, 0);
+          if (slot >= 0) {
+            __threadfence_block();
+            const uint32_t hlo = s_hlo[slot], hhi = s_hhi[slot];
+            wc_slab(J.g, hlo, hhi, s_hthr[slot], (hlo >> 2) + (uint32_t)sl * WC_SLAB, (hhi + 3) >> 2, J.rk, sc, lane,
+                    stage, dr, visit);
+            __syncwarp();
+            if (lane == 0) {
+              __threadfence_block();  // new queue entries and splits before letting go
+              atomicSub(&s_active, 1);
+            }
+            idle = 0;
+            continue;
+          }
+          // (b) up to 32 queued nodes
+          int h = 0, cnt = 0;
+          if (lane == 0) {
+            atomicAdd(&s_active, 1);
+            for (;;) {
+              h = *(volatile int*)&s_head;
+              const int avail = min(*(volatile int*)&s_tail, qlim) - h;
+              cnt = avail < 32 ? avail : 32;
+              if (cnt <= 0 || atomicCAS(&s_head, h, h + cnt) == h) break;
+            }
+            if (cnt <= 0) atomicSub(&s_active, 1);
+          }
+          h = __shfl_sync(FULL_MASK, h, 0);
+          cnt = __shfl_sync(FULL_MASK, cnt, 0);
+          if (cnt > 0) {
+            int32_t v = -1;
+            if (lane < cnt) {
+              // the slot's writer has reserved it; wait (briefly) for its store
+              for (long long w = 0; (v = *(volatile int32_t*)&Q[h + lane]) < 0; ++w) {
+                if (w > (1ll << 22)) {
+                  atomicExch(&J.ctr->error, 1u);
+                  v = -1;
+                  break;
+                }
+              }
+            }
+            expand_ic<true>(J.g, v, J.rk, sc, lane, stage, ev, dr, 4 * (int)WC_SLAB - 1, known, visit, take_split);
+            __syncwarp();
+            if (lane == 0) {
+              __threadfence_block();  // new queue entries and splits before letting go
+              atomicSub(&s_active, 1);
+            }
+            idle = 0;
+            continue;
+          }
+          // (c) nothing to claim: the sample is done once no warp holds work
+          int done = 0;
+          if (lane == 0 && *(volatile int*)&s_active == 0) {
+            __threadfence_block();
+            done = *(volatile int*)&s_head >= min(*(volatile int*)&s_tail, qlim);
+            const int ns2 = min(*(volatile int*)&s_nsplit, CTA_HEAVY_CAP);
+            for (int i = 0; i < ns2 && done; ++i) {
+              const int ns = *(volatile int*)&s_hpref[i];
+              if (ns == 0 || *(volatile int*)&s_hnext_slab[i] < ns) done = 0;
+            }
+          }
+          if (__shfl_sync(FULL_MASK, done, 0)) break;
+          if (++idle > (1ll << 24)) {  // far longer than any sample: give up and report
+            if (lane == 0) atomicExch(&J.ctr->error, 1u);
+            break;
+          }
+          __nanosleep(64);
+        }
+        __syncthreads();
+      } else {
+      const int wid = tid >> 5;
       auto take_heavy = [&](int32_t, uint32_t lo, uint32_t hi, int) -> int {
         const int slot = atomicAdd(&s_nheavy, 1);
         if (slot >= CTA_HEAVY_CAP) return 0;  // list full: this warp expands it itself
         s_hlo[slot] = lo;
         s_hhi[slot] = hi;
-        if (WC) s_hthr[slot] = wc_threshold(hi - lo);
         ev += hi - lo;
         return HEAVY_SKIP;
       };
-      const int wid = tid >> 5, nwarp = nthr >> 5;
       if (tid == 0) s_nheavy = 0;
       int lvl_begin = 0, lvl_end = 1;
       for (;;) {
@@ -687,16 +837,12 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
           if (b >= lvl_end) break;
           const int cnt = min(32, lvl_end - b);
           const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
-          if (expand_ic<WC>(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy))
+          if (expand_ic<false>(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy))
             break;
         }
         __syncthreads();
         const int nh = min(s_nheavy, CTA_HEAVY_CAP);
-        if (WC && nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
-          // every warp takes slabs wid, wid + nwarp, ... of each heavy list in turn
-          for (int i = 0; i < nh; ++i)
-            if (wc_walk(J.g, s_hlo[i], s_hhi[i], s_hthr[i], wid, nwarp, J.rk, sc, lane, stage, dr, visit)) break;
-        } else if (nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
+        if (nh > 0 && !s_hit && !(KIND == 1 && s_tail > qcap)) {
           // groups of the heavy in-lists, dealt to all warps 32 at a time
           if (wid == 0) {
             int carry = 0;
@@ -725,8 +871,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
               if (it + step < nh && s_hpref[it + step] <= q) it += step;
             const uint32_t olo = s_hlo[it], ohi = s_hhi[it];
             const uint32_t grp = (olo >> 2) + (uint32_t)(q - s_hpref[it]);
-            if (process_slab<WC>(J.g, q < htotal, grp, olo, ohi, WC ? s_hthr[it] : 0u, J.rk, sc, lane, stage, dr,
-                                 known, visit))
+            if (process_slab<false>(J.g, q < htotal, grp, olo, ohi, 0u, J.rk, sc, lane, stage, dr, known, visit))
               break;
           }
         }
@@ -736,8 +881,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
         lvl_end = s_tail;
         __syncthreads();
       }
-      (void)wid;
-      (void)nwarp;
+      }
     } else if (tid == 0) {
       const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_LT, J.stream, j));
       int32_t cur = root;
@@ -787,6 +931,8 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
         J.big2_list[b] = j;
       }
       for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
+      if (WC && J.model == 0)
+        for (int64_t i = tid; i < qcap; i += nthr) Q[i] = -1;  // the queue's "not written yet" marks
       __syncthreads();
       continue;
     }
@@ -812,11 +958,18 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
       J.hit[j - J.j0] = s_hit ? 1 : 0;
     }
     if (tid == 0) nv += (unsigned long long)tail;
-    // reset the visited bits of this sample only
+    // reset the visited bits of this sample only (and, for the weighted-cascade
+    // IC path, the queue's "not written yet" marks)
+    const bool marks = WC && J.model == 0;
     if ((int64_t)tail * 8 < J.bitmap_words) {
-      for (int i = tid; i < tail; i += nthr) bits[Q[i] >> 5] = 0u;
+      for (int i = tid; i < tail; i += nthr) {
+        bits[Q[i] >> 5] = 0u;
+        if (marks) Q[i] = -1;
+      }
     } else {
       for (int64_t i = tid; i < J.bitmap_words; i += nthr) bits[i] = 0u;
+      if (marks)
+        for (int i = tid; i < tail; i += nthr) Q[i] = -1;
     }
     __syncthreads();
   }
@@ -827,13 +980,15 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, 1) k_sample_cta(Sample
 
 constexpr int64_t SMEM_BITMAP_MAX_BYTES = 192 * 1024;
 
-LaunchCfg sampler_config(const GraphView& g, int model) {
+LaunchCfg sampler_config(const GraphView& g, int model, bool wc) {
   LaunchCfg c;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 0;
-  if (model == 0)
+  if (model == 0 && wc)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE, 0, true>, WT_WARPS * 32, 0);
+  else if (model == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_warp_ic<MODE_STORE, 0, false>, WT_WARPS * 32,
                                                   0);
   else
@@ -848,8 +1003,11 @@ LaunchCfg sampler_config(const GraphView& g, int model) {
   if (!c.cta_smem_bitmap) {
     // global bitmap: many small CTAs first, a few full-size ones for the largest sets
     int small_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, false>, 256,
-                                                  0);
+    if (model == 0 && wc)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, true>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, false>, 256,
+                                                    0);
     if (small_per_sm < 1) small_per_sm = 1;
     c.small_blocks = c.num_sms * small_per_sm;
     c.small_qcap = (int)std::min<int64_t>(g.n, 1 << 20);

@@ -125,7 +125,11 @@ struct ssa_server {
         r->t_start = now_s();
       }
       ssa_status s = SSA_OK;
-      if (!solvers[(size_t)r->graph]) s = ssa_solver_create(graphs[(size_t)r->graph], st, 0, &solvers[(size_t)r->graph]);
+      if (!solvers[(size_t)r->graph]) {
+        s = ssa_solver_create(graphs[(size_t)r->graph], st, 0, &solvers[(size_t)r->graph]);
+        // each round's index, greedy and stare as one CUDA graph, reused by later requests
+        if (s == SSA_OK) s = ssa_solver_set_graphs(solvers[(size_t)r->graph], 1);
+      }
       if (s == SSA_OK) {
         r->seeds.assign((size_t)r->p.k, -1);
         r->trace.assign(64, ssa_round{});

@@ -224,6 +224,29 @@ def test_solver_reuse_same_answers():
     assert np.array_equal(a.seeds, b.seeds) and a.trace == b.trace == c.trace
 
 
+def test_round_graphs_and_kept_workspaces_same_answers():
+    # Each round's index, greedy and stare as one CUDA graph, patched into the
+    # executable the solver keeps per round: the same seeds, traces and counts as
+    # separate launches and as the oracle, over repeated solves of different
+    # models, algorithms, k and WRIS on one solver (kept scratch, reused graphs)
+    el = inputs.rmat(13, 1 << 16, seed=8)
+    og, gg = _pair(el)
+    b = inputs.zipf_benefit(el.n, 1.2, seed=2)
+    plain, graphed = P.Solver(gg), P.Solver(gg).set_graphs(True)
+    cases = [(1, 0, 10, 3, None), (1, 0, 10, 4, None), (1, 1, 20, 5, None), (0, 0, 10, 6, None),
+             (1, 0, 50, 7, b), (0, 1, 5, 8, None), (1, 0, 10, 3, None)]
+    for algo, model, k, seed, ben in cases:
+        o = oracle.solve(og, algo, model, k, 0.1, 1.0 / el.n, seed, benefit=ben)
+        r0 = plain.solve(algo, model, k, 0.1, 1.0 / el.n, seed, benefit=ben)
+        r1 = graphed.solve(algo, model, k, 0.1, 1.0 / el.n, seed, benefit=ben)
+        _same_solution(o, r0)
+        _same_solution(o, r1)
+        assert r0.n_rr == r1.n_rr and r0.pool_entries == r1.pool_entries
+        assert r0.edge_visits == r1.edge_visits and r0.kernel_launches == r1.kernel_launches
+    plain.free()
+    graphed.free()
+
+
 def test_bad_solve_arguments():
     el = c1_edges()
     gg = P.ssa_load_graph(el.n, el.src, el.dst, None, P.SSA_W_TRIVALENCY)
@@ -258,6 +281,29 @@ def test_sampler_tiers_give_identical_sets(mid_cap, heavy):
         for mode_lam in (20.5, 300.0):  # hit-test mode through every tier
             assert P.ssa_estimate_inf(gg, oracle.IC, 4, 2, seeds, mode_lam, 5000) == \
                 oracle.estimate_inf(og, oracle.IC, 4, 2, seeds, mode_lam, 5000)[:2]
+
+
+@pytest.mark.parametrize("scale,m_draw,small_q", [(14, 1 << 18, 0), (21, 1 << 24, 0), (21, 1 << 24, 256)])
+def test_wc_cta_tier_sets(scale, m_draw, small_q):
+    # Weighted-cascade IC through the CTA tier's barrier-free BFS: shared-memory
+    # bitmap (2^14 nodes) and global bitmap (2^21 nodes).  Handing samples over
+    # at in-lists of 64 groups sends hubs through the split table; a 256-entry
+    # small-CTA queue sends sets of more than 256 nodes on to the full-size CTAs.
+    # Stored sets and hit-test mode both equal the oracle.
+    el = inputs.rmat(scale, m_draw, seed=7)
+    og, gg = _pair(el)
+    P.ssa_set_queue_tuning(gg, small_q)
+    for mid, heavy in ((0, 64), (0, 0x7FFFFFFF), (16384, 64)):
+        P.ssa_set_tuning(gg, mid, heavy)
+        op, gp = _check_pool(og, gg, oracle.IC, seed=5, stream=0, N=2000)
+        seeds, _, _ = op.max_coverage(2000, 4)
+        for lam in (15.5, 400.0):
+            assert P.ssa_estimate_inf(gg, oracle.IC, 5, 3, seeds, lam, 3000) == \
+                oracle.estimate_inf(og, oracle.IC, 5, 3, seeds, lam, 3000)[:2]
+    off, _ = op.arrays()
+    if small_q:
+        assert np.diff(off).max() > small_q  # the full-size stage was needed
+    P.ssa_set_queue_tuning(gg, 0)
 
 
 def test_autotune_picks_a_candidate():
