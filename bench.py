@@ -365,7 +365,9 @@ def run_serving(args):
     __graft_entry__.build()
     import paper_1605_07990_gb300 as P
     torch.cuda.set_device(0)
+    P.ssa_set_greedy_mode(args.greedy_mode)
     line = serving(P, args.queries, args.slots)
+    line["greedy_mode"] = args.greedy_mode
     line.update({"metric": "serving queries/s and p50/p99 latency", "unit": "queries/s",
                  "value": line["server"]["queries_per_s"], "higher_is_better": True, "n_gpus": 1,
                  "data": "synthetic"})
@@ -464,11 +466,15 @@ def main():
                     help="profiling case: only sample this many RR sets of the workload into a pool")
     ap.add_argument("--then-greedy", type=int, default=0,
                     help="with --sample-only: also index the pool and run greedy Max-Coverage for this k")
+    ap.add_argument("--tune", default="",
+                    help="with --sample-only: IC sampler hand-overs MID_CAP,HEAVY_GROUPS (ssa_set_tuning)")
     ap.add_argument("--serving", action="store_true", help="the Poisson serving mix instead of the solve bench")
     ap.add_argument("--queries", type=int, default=2000, help="queries of --serving")
     ap.add_argument("--serving-queries", type=int, default=120,
                     help="queries of the serving mix measured after the solve bench (0: skip)")
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--greedy-mode", type=int, default=0,
+                    help="greedy launch shape (ssa_set_greedy_mode): 0 by pool size, 1 grid, 2 cluster")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -499,9 +505,14 @@ def main():
         og_thread = OracleGraph(el, weighting)
         og_thread.start()
     if args.sample_only:
+        if args.tune:
+            mid, heavy = (int(x) for x in args.tune.split(","))
+            P.ssa_set_tuning(g, mid, heavy)
+        t0 = time.perf_counter()
         pool = P.Pool(g, model, seed=1, stream=0).grow(args.sample_only)
         torch.cuda.synchronize()
-        out = {"sample_only": args.sample_only, "pool": pool.info()}
+        out = {"sample_only": args.sample_only, "pool": pool.info(), "seconds": time.perf_counter() - t0,
+               "tune": args.tune}
         if args.then_greedy:
             _, gains, cov = pool.max_coverage(args.sample_only, args.then_greedy)
             out["greedy"] = {"k": args.then_greedy, "cov": int(cov)}
@@ -567,7 +578,8 @@ def main():
         ta = time.perf_counter()
         g2 = P.ssa_load_graph(el.n, src_np, dst_np, None, weighting, 1)
         tb = time.perf_counter()
-        r = P.ssa_solve(g2, algo, model, k, eps, delta, 500 + seed_of(s))
+        # the timed steps' own seeds, so both legs draw the same RR sets
+        r = P.ssa_solve(g2, algo, model, k, eps, delta, seed_of(s))
         tc = time.perf_counter()
         rr_e2e += r.n_rr
         g2.free()
@@ -580,7 +592,8 @@ def main():
                        "d2h_bytes_per_step": int(k * 4 + 64), "steps": args.e2e_steps,
                        "includes": "graph upload + device CSR build + solve (first solve on a new graph handle "
                                    "runs the sampler autotuner) + seeds to host",
-                       "load_s_per_step": t_load / args.e2e_steps, "solve_s_per_step": t_solve / args.e2e_steps}
+                       "load_s_per_step": t_load / args.e2e_steps, "solve_s_per_step": t_solve / args.e2e_steps,
+                       "seeds": "the first e2e steps use the timed steps' Philox seeds"}
 
     if args.extra_steps > 0 and name != EXTRA:
         el2, w2, _, _, _, _ = make_graph_inputs(EXTRA)

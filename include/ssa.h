@@ -145,11 +145,19 @@ ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_sampl
                         double* pilot_ms);
 ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap, int32_t heavy_groups);
 /* Queue capacity of the CTA tier's first stage when the n-bit visited bitmap
- * lives in global memory (n/8 above 192 KB): 256-thread CTAs keep sets of up to
+ * lives in global memory (n/8 above 192 KB): 128-thread CTAs keep sets of up to
  * small_queue nodes, and full-size CTAs redo larger sets.  0 restores the
  * default min(n, 2^20).  Applies to sampler scratch created afterwards (new
  * pools and solvers); results never depend on it.  SSA_E_ARG if negative. */
 ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue);
+
+/* Process-wide choice of the greedy kernel's launch shape (results never
+ * depend on it): 0 (default) runs all picks of a Max-Coverage over at most 2^26
+ * pool entries in one thread-block cluster of 16 (or 8) blocks, synchronised by
+ * the hardware cluster barrier, and larger pools in a cooperative grid of one
+ * block per SM; 1 always uses the cooperative grid; 2 always a cluster.  Applies
+ * to launches after the call.  SSA_E_ARG for other values. */
+ssa_status ssa_set_greedy_mode(int32_t mode);
 
 /* Process-wide bound on the polls of each device-side wait: the grid barriers
  * of the greedy kernel (ssa_max_coverage and every solve).  A wait that reaches

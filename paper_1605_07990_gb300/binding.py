@@ -77,6 +77,7 @@ EXPORTS = {
     "ssa_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "ssa_set_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "ssa_set_wait_polls": (C.c_int, [C.c_int64]),
+    "ssa_set_greedy_mode": (C.c_int, [C.c_int32]),
     "ssa_set_queue_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
@@ -220,6 +221,11 @@ def ssa_set_tuning(g: Graph, mid_cap, heavy_groups=0x7FFFFFFF):
 
 def ssa_set_queue_tuning(g: Graph, small_queue=0):
     _check(lib().ssa_set_queue_tuning(g.h, int(small_queue)))
+
+
+def ssa_set_greedy_mode(mode=0):
+    """0: cluster or grid by pool size; 1: always the cooperative grid; 2: always a cluster."""
+    _check(lib().ssa_set_greedy_mode(int(mode)))
 
 
 def ssa_set_wait_polls(polls=0):

@@ -1593,6 +1593,12 @@ ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue) {
   return SSA_OK;
 }
 
+ssa_status ssa_set_greedy_mode(int32_t mode) {
+  if (mode < 0 || mode > 2) return fail(SSA_E_ARG, "greedy mode must be 0, 1 or 2");
+  set_greedy_mode(mode);
+  return SSA_OK;
+}
+
 ssa_status ssa_set_wait_polls(int64_t polls) {
   if (polls < 0) return fail(SSA_E_ARG, "polls must be >= 0");
   g_wait_polls.store(polls == 0 ? GREEDY_DEFAULT_WAIT_POLLS : (long long)polls, std::memory_order_relaxed);

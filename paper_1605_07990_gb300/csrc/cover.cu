@@ -9,6 +9,11 @@
 // maximum packed key (gain+1)<<32 | ~v (largest gain, then smallest id; picked
 // nodes keyed to 0), then warps decrement the gains of the members of each
 // newly covered set.
+#include <atomic>
+#include <mutex>
+
+#include <cooperative_groups.h>
+
 #include "device.cuh"
 
 namespace ssa {
@@ -149,7 +154,7 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long x, un
 
 // sync layout: arrival count, release word and timeout flag on separate
 // 128-byte lines so that polling does not contend with the arrivals.
-constexpr int SYNC_COUNT = 0, SYNC_GEN = 32, SYNC_ERR = 64, SYNC_CHUNKS = 96, SYNC_WORDS = 128;
+constexpr int SYNC_COUNT = 0, SYNC_GEN = 32, SYNC_ERR = 64, SYNC_CHUNKS = 96;
 constexpr int DEC_CHUNK = 2048;    // covered sets longer than this are decremented in chunks by all warps
 constexpr int CACHE_MAX = 8192;    // greedy candidate cache entries
 constexpr int ARGMAX_STRIDE = 16;  // argmax slots one 128-byte line apart
@@ -168,15 +173,19 @@ constexpr int ACC_DONE = 64, ACC_QUEUED = 64 + 1024;
 // releases it; all threads get it in `info`.  A wait gives up after `limit`
 // polls (about a second by default), sets sync[SYNC_ERR] and returns false;
 // that block then leaves the kernel, and the others give up at their next
-// barrier, which it never reaches.
+// barrier, which it never reaches.  Every block passes every barrier in the
+// same order, so each keeps the current sense in its shared `phase` (0 at
+// launch, when the release word is zero) instead of reading it back.
 template <class F>
-__device__ __forceinline__ bool grid_barrier(unsigned int* sync, long long limit, F&& f, unsigned long long& info) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* sync, unsigned int* phase, long long limit, F&& f,
+                                             unsigned long long& info) {
   __shared__ unsigned long long s_info;
   __shared__ unsigned int s_last, s_ok, s_sense;
   volatile unsigned long long* gw = reinterpret_cast<volatile unsigned long long*>(sync + SYNC_GEN);
   __syncthreads();
   if (threadIdx.x == 0) {
-    s_sense = (unsigned int)(*gw & 1ull);
+    s_sense = *phase;
+    *phase = s_sense ^ 1u;
     s_ok = 1;
     __threadfence();
     const bool last = atomicAdd(sync + SYNC_COUNT, 1u) + 1u == gridDim.x;
@@ -213,6 +222,33 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* sync, long long limit
   return s_ok != 0u;
 }
 
+// The greedy's barrier.  GRID: grid_barrier across a cooperative launch.
+// CLUSTER: the whole greedy runs in one thread-block cluster, so the barrier is
+// the hardware cluster barrier; block 0 then computes f() and the others read
+// its result from block 0's shared memory (distributed shared memory) after a
+// second cluster barrier.  A cluster barrier always completes (the cluster's
+// blocks are scheduled together), so it has no bound to reach.
+template <bool CLUSTER, class F>
+__device__ __forceinline__ bool greedy_barrier(const GreedyJob& J, unsigned int* phase, F&& f,
+                                               unsigned long long& info) {
+  if constexpr (!CLUSTER) {
+    return grid_barrier(J.sync, phase, J.wait_polls, f, info);
+  } else {
+    namespace cg = cooperative_groups;
+    __shared__ unsigned long long s_res;
+    cg::cluster_group cluster = cg::this_cluster();
+    __threadfence();  // this block's global writes and atomics before the others look
+    cluster.sync();
+    if (cluster.block_rank() == 0) {
+      const unsigned long long r = f();
+      if (threadIdx.x == 0) s_res = r;
+    }
+    cluster.sync();
+    info = *cluster.map_shared_rank(&s_res, 0);
+    return true;
+  }
+}
+
 // Packed argmax key: larger gain first, then smaller id; picked nodes (negative
 // gain) key to 0.  With gains below 2^31 - 1 and ids below 2^31, keys stay
 // below 2^62, under the barrier payload's PENDING flag.
@@ -241,14 +277,15 @@ __device__ __forceinline__ void decrement_members(int32_t* cnt, const int32_t* m
 // its own into one of three slots by atomicMax, and the barrier publishes the
 // slot.  Argmax number a uses slot a % 3; block 0 clears slot (a + 2) % 3 after
 // the barrier, which no block writes before the next barrier has completed.
+template <bool CLUSTER>
 __device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long long& best, unsigned long long* s_red,
-                                            int& n_argmax) {
+                                            int& n_argmax, unsigned int* phase) {
   best = block_max(best, s_red);
   const int slot = n_argmax % 3;
   n_argmax += 1;
   unsigned long long* at = J.argmax + slot * ARGMAX_STRIDE;
   if (threadIdx.x == 0 && best != 0ull) atomicMax(at, best);
-  if (!grid_barrier(J.sync, J.wait_polls, [&] { return __ldcg(at); }, best)) return false;
+  if (!greedy_barrier<CLUSTER>(J, phase, [&] { return __ldcg(at); }, best)) return false;
   if (blockIdx.x == 0 && threadIdx.x == 0) J.argmax[((slot + 2) % 3) * ARGMAX_STRIDE] = 0ull;
   return true;
 }
@@ -275,6 +312,7 @@ __device__ __forceinline__ bool grid_argmax(const GreedyJob& J, unsigned long lo
 // recount instead: gains are rebuilt from the uncovered sets, which costs
 // fewer atomics than the decrements would.  Barrier waits are bounded
 // (sync[SYNC_ERR] on timeout).
+template <bool CLUSTER>
 __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   __shared__ unsigned long long s_red[32];
   __shared__ int64_t s_lo[GREEDY_MAX_LISTS], s_hi[GREEDY_MAX_LISTS];
@@ -283,6 +321,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   __shared__ unsigned int s_buf[CACHE_MAX > HBINS ? CACHE_MAX : HBINS];
   __shared__ long long s_scan[32], s_scan_tot;
   __shared__ unsigned long long s_cov_e, s_queued_e;  // entries of the sets this block covered / queued
+  __shared__ unsigned int s_phase;                     // sense of the next grid barrier
   unsigned long long my_done = 0, my_queued = 0;      // thread 0: this block's slot values
   unsigned int* s_hist = s_buf;
   int32_t* s_cache = reinterpret_cast<int32_t*>(s_buf);
@@ -293,6 +332,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
   const int64_t n4 = J.n_pad >> 2;
   const int4* c4 = reinterpret_cast<const int4*>(J.cnt);
   int n_argmax = 0;
+  if (threadIdx.x == 0) s_phase = 0u;  // the host zeroed the release word (sense 0)
   // Rebuild policy (every block tracks the same values): the first pick only
   // scans; a rebuild needs at least REBUILD_MIN picks left; a cache that served
   // fewer than REBUILD_MIN picks, or a rebuild that found no threshold,
@@ -333,7 +373,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
             const unsigned long long key = gain_key(__ldcg(J.cnt + v), (uint32_t)v);
             best = key > best ? key : best;
           }
-          if (!grid_argmax(J, best, s_red, n_argmax)) return;
+          if (!grid_argmax<CLUSTER>(J, best, s_red, n_argmax, &s_phase)) return;
           valid = true;
         }
       } else if (fused_ok) {
@@ -385,7 +425,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         for (int t = threadIdx.x; t < HBINS; t += blockDim.x)
           if (s_hist[t]) atomicAdd(h + t, s_hist[t]);
       }
-      if (!grid_argmax(J, best, s_red, n_argmax)) return;
+      if (!grid_argmax<CLUSTER>(J, best, s_red, n_argmax, &s_phase)) return;
       if (rebuild) {
         // g* = floor + the smallest bin b with at most CACHE_MAX nodes in
         // bins >= b: a descending block scan of the merged histogram (thread t
@@ -524,7 +564,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         J.argmax[ACC_QUEUED + blockIdx.x] = my_queued;
       }
     }
-    if (!grid_barrier(J.sync, J.wait_polls, [&]() -> unsigned long long {
+    if (!greedy_barrier<CLUSTER>(J, &s_phase, [&]() -> unsigned long long {
           const unsigned int m = __ldcg(chunks);
           if (m > 0u) {
             // entries still in uncovered sets after this pick, against the queued ones
@@ -558,14 +598,14 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         reinterpret_cast<int4*>(J.cnt)[q] = c;
       }
       unsigned long long unused = 0;
-      if (!grid_barrier(J.sync, J.wait_polls, [] { return 0ull; }, unused)) return;
+      if (!greedy_barrier<CLUSTER>(J, &s_phase, [] { return 0ull; }, unused)) return;
       for (int64_t j = warp; j < J.n_sets; j += nwarps) {
         if (__ldcg(J.covered + j)) continue;
         const int32_t* mem = J.pool_nodes + J.set_start[j];
         const int32_t len = J.set_len[j];
         for (int t = lane; t < len; t += 32) atomicAdd(J.cnt + __ldg(mem + t), 1);
       }
-      if (!grid_barrier(J.sync, J.wait_polls, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
+      if (!greedy_barrier<CLUSTER>(J, &s_phase, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
     } else if (pay & PENDING) {
       const int64_t nchunks = (int64_t)(pay & (RECOUNT - 1ull));
       for (int64_t c = warp; c < nchunks; c += nwarps) {
@@ -575,10 +615,15 @@ __global__ void __launch_bounds__(1024, 1) k_greedy(GreedyJob J) {
         const int32_t cnt = min(DEC_CHUNK, len - from);
         decrement_members(J.cnt, J.pool_nodes + J.set_start[j] + from, cnt, lane);
       }
-      if (!grid_barrier(J.sync, J.wait_polls, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
+      if (!greedy_barrier<CLUSTER>(J, &s_phase, [&]() -> unsigned long long { return fuse ? cache_argmax() : 0ull; }, pay)) return;
     }
     fused_key = pay;
     fused_ok = fuse;
+  }
+  if constexpr (CLUSTER) {
+    // no block may leave while another can still read its shared memory: the
+    // payload of the last barrier lives in block 0's
+    cooperative_groups::this_cluster().sync();
   }
 }
 
@@ -736,10 +781,68 @@ cudaError_t launch_scatter_index(const int32_t* nodes, const int32_t* samp, int6
   return cudaGetLastError();
 }
 
+namespace {
+// Largest cluster of 1024-thread greedy blocks the device can schedule (16 or
+// 8), 0 if none; computed once per process.
+int greedy_cluster_size() {
+  static int size = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (size >= 0) return size;
+  size = 0;
+  if (cudaFuncSetAttribute(k_greedy<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    (void)cudaGetLastError();
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(1024);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_greedy<true>, &cfg) == cudaSuccess && clusters >= 1) {
+      size = c;
+      break;
+    }
+    (void)cudaGetLastError();
+  }
+  return size;
+}
+std::atomic<int> g_greedy_mode{0};
+}  // namespace
+
+void set_greedy_mode(int mode) { g_greedy_mode.store(mode); }
+
 cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used) {
+  // Pools of up to GREEDY_CLUSTER_ENTRIES entries: all picks in one thread-block
+  // cluster (hardware cluster barriers, a fraction of a microsecond); larger
+  // pools, whose first picks decrement millions of gains, use one 1024-thread
+  // block per SM in a cooperative launch.
+  const int mode = g_greedy_mode.load();
+  const int csize = mode == 1 ? 0 : greedy_cluster_size();
+  if (csize > 0 && (mode == 2 || J.total_entries <= GREEDY_CLUSTER_ENTRIES)) {
+    *blocks_used = csize;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_greedy<true>, J);
+  }
   // one 1024-thread block per SM: the fewest barrier arrivals with a full machine
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy, 1024, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy<false>, 1024, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int blocks = num_sms;
@@ -757,12 +860,12 @@ cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int*
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_greedy, J);
+  return cudaLaunchKernelEx(&cfg, k_greedy<false>, J);
 }
 
 cudaError_t device_code_version(int* binary, int* ptx) {
   cudaFuncAttributes a{};
-  const cudaError_t e = cudaFuncGetAttributes(&a, k_greedy);
+  const cudaError_t e = cudaFuncGetAttributes(&a, k_greedy<false>);
   if (e != cudaSuccess) return e;
   *binary = a.binaryVersion;
   *ptx = a.ptxVersion;

@@ -172,8 +172,12 @@ struct GreedyJob {
 constexpr long long GREEDY_DEFAULT_WAIT_POLLS = 1ll << 22;  // about a second with the poll back-off
 // Process-wide poll limit of the greedy kernel's grid-barrier waits (ssa_set_wait_polls).
 long long greedy_wait_polls();
-// All k picks in one cooperative launch (bounded grid barriers).
+// All k picks in one launch: one thread-block cluster for pools of up to
+// GREEDY_CLUSTER_ENTRIES entries, else a cooperative grid (bounded grid barriers).
+constexpr unsigned long long GREEDY_CLUSTER_ENTRIES = 1ull << 26;
 cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used);
+// 0: by pool size (default); 1: always the cooperative grid; 2: always a cluster (when the device has one)
+void set_greedy_mode(int mode);
 cudaError_t launch_add_counts(int32_t* total, const int32_t* add, int64_t n, cudaStream_t st, int num_sms);
 // SASS and PTX versions (major*10 + minor) of the device code the CUDA runtime loaded for this library
 cudaError_t device_code_version(int* binary, int* ptx);

@@ -30,6 +30,7 @@ constexpr int LT_QCAP = 1024;    // largest LT walk kept in the warp tier
 constexpr int STAGE = 128;       // live candidates of one slab (32 lanes x 4 edges)
 constexpr int CTA_HEAVY_GROUPS = 512;    // the CTA tier splits longer in-lists over all its warps
 constexpr int CTA_HEAVY_CAP = 256;       // heavy in-lists per level shared this way
+constexpr int SMALL_CTA_THREADS = 128;   // CTAs of the first stage when the visited bitmap is in global memory
 
 constexpr uint32_t PHILOX_M0 = 0xD2511F53u, PHILOX_M1 = 0xCD9E8D57u;
 
@@ -305,6 +306,10 @@ __device__ __forceinline__ bool wc_walk(const GraphView& g, uint32_t lo, uint32_
     if (wc_slab(g, lo, hi, thr, b, g1, rk, sc, lane, stage, draws, visit)) return true;
   return false;
 }
+
+// In the weighted-cascade CTA tier, in-lists of more than this many groups are
+// split into slabs that any warp of the CTA takes.
+constexpr int WC_SPLIT_GROUPS = 2 * (int)WC_SLAB - 1;
 
 // In-lists of at least this many 4-edge groups are walked by the whole warp
 // alone (weighted cascade): no owner search per group.
@@ -612,8 +617,9 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_lt(SampleJob J) {
 //         a set that outgrows the queue goes on to KIND 2.
 // KIND 2: full-size CTAs (global bitmap, queue of n entries) for those sets.
 template <int MODE, bool SMEM_BITMAP, int KIND, bool WC>
-__global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, KIND == 1 ? 4 : 1) k_sample_cta(SampleJob J) {
-  constexpr int WARPS = KIND == 1 ? 8 : 32;
+__global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 1 ? 1024 / SMALL_CTA_THREADS : 1)
+    k_sample_cta(SampleJob J) {
+  constexpr int WARPS = KIND == 1 ? SMALL_CTA_THREADS / 32 : 32;
   extern __shared__ __align__(16) uint32_t s_bits[];
   __shared__ long long s_item;
   __shared__ int s_tail, s_next, s_hit, s_ok;
@@ -784,7 +790,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 256 : 1024, KIND == 1 ? 4 : 1) k_s
                 }
               }
             }
-            expand_ic<true>(J.g, v, J.rk, sc, lane, stage, ev, dr, 4 * (int)WC_SLAB - 1, known, visit, take_split);
+            expand_ic<true>(J.g, v, J.rk, sc, lane, stage, ev, dr, WC_SPLIT_GROUPS, known, visit, take_split);
             __syncwarp();
             if (lane == 0) {
               __threadfence_block();  // new queue entries and splits before letting go
@@ -1004,10 +1010,11 @@ LaunchCfg sampler_config(const GraphView& g, int model, bool wc) {
     // global bitmap: many small CTAs first, a few full-size ones for the largest sets
     int small_per_sm = 0;
     if (model == 0 && wc)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, true>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, true>,
+                                                    SMALL_CTA_THREADS, 0);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, false>, 256,
-                                                    0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_sample_cta<MODE_STORE, false, 1, false>,
+                                                    SMALL_CTA_THREADS, 0);
     if (small_per_sm < 1) small_per_sm = 1;
     c.small_blocks = c.num_sms * small_per_sm;
     c.small_qcap = (int)std::min<int64_t>(g.n, 1 << 20);
@@ -1061,7 +1068,7 @@ static cudaError_t launch_cta_t(const SampleJob& J, const LaunchCfg& c, cudaStre
     if (e != cudaSuccess) return e;
     k_sample_cta<MODE, true, 0, WC><<<c.cta_blocks, c.cta_threads, smem, st>>>(J);
   } else {
-    k_sample_cta<MODE, false, 1, WC><<<c.small_blocks, 256, 0, st>>>(J);
+    k_sample_cta<MODE, false, 1, WC><<<c.small_blocks, SMALL_CTA_THREADS, 0, st>>>(J);
     k_sample_cta<MODE, false, 2, WC><<<c.cta_blocks, c.cta_threads, 0, st>>>(J);
   }
   return cudaGetLastError();

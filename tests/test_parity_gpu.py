@@ -103,7 +103,7 @@ def test_rr_sets_empty_graph_and_isolated():
     assert all(len(s) == 1 for s in gp.sets())
 
 
-def test_counts_greedy_coverage_c1():
+def test_counts_greedy_coverage_c1(greedy_mode):
     og, gg = _pair(c1_edges())
     N = 2 * 2806
     op, gp = _check_pool(og, gg, oracle.IC, seed=1, stream=0, N=N)
@@ -118,7 +118,7 @@ def test_counts_greedy_coverage_c1():
         assert op.coverage(a, b, S) == gp.coverage(a, b - a, S)
 
 
-def test_greedy_k_equals_n():
+def test_greedy_k_equals_n(greedy_mode):
     el = inputs.rmat(6, 300, seed=1)
     og, gg = _pair(el)
     op, gp = _check_pool(og, gg, oracle.IC, seed=2, stream=0, N=500)
@@ -129,7 +129,7 @@ def test_greedy_k_equals_n():
 
 
 @pytest.mark.parametrize("model", [oracle.IC, oracle.LT])
-def test_greedy_long_k_candidate_cache(model):
+def test_greedy_long_k_candidate_cache(model, greedy_mode):
     # thousands of picks on a 2^15-node graph: the greedy kernel rebuilds its
     # candidate cache many times, misses it, and falls back to full scans
     el = inputs.rmat(15, 1 << 18, seed=11)
@@ -144,7 +144,7 @@ def test_greedy_long_k_candidate_cache(model):
         assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
 
 
-def test_greedy_long_sets_queue_and_recount():
+def test_greedy_long_sets_queue_and_recount(greedy_mode):
     # every edge live on a 2^13-node R-MAT: sets are whole reverse-reachable
     # sets, thousands of nodes sharing one core, so covering them goes through
     # the queued-chunk path: the first pick recounts the gains, later ones drain
@@ -161,7 +161,7 @@ def test_greedy_long_sets_queue_and_recount():
         assert np.array_equal(os_, gs_) and np.array_equal(og_, gg_) and oc == gc
 
 
-def test_greedy_flat_gains_ties():
+def test_greedy_flat_gains_ties(greedy_mode):
     # an edgeless graph: every RR set is its root alone, gains are small and
     # heavily tied, so the smallest-id tie rule decides most picks
     el = inputs.edges(20_000, [])
@@ -183,6 +183,14 @@ def test_estimate_inf(model):
         oT, oh, _ = oracle.estimate_inf(og, model, 1, 5, S, lam2, t_max)
         gT, gh = P.ssa_estimate_inf(gg, model, 1, 5, S, lam2, t_max)
         assert (oT, oh) == (gT, gh)
+
+
+@pytest.fixture(params=[1, 2], ids=["grid", "cluster"])
+def greedy_mode(request):
+    # the greedy kernel's two launch shapes: a cooperative grid and one thread-block cluster
+    P.ssa_set_greedy_mode(request.param)
+    yield request.param
+    P.ssa_set_greedy_mode(0)
 
 
 def _same_solution(o, g):

@@ -2,7 +2,9 @@
 
 The greedy Max-Coverage kernel (Algorithm 2, all k picks in one cooperative
 launch) synchronises its blocks with grid barriers whose waits give up after a
-bounded number of polls.  Here the bound is set to one poll, so ordinary
+bounded number of polls.  Here the greedy is held to that cooperative-grid
+shape (small pools otherwise run in one thread-block cluster, whose hardware
+barrier needs no bound) and the bound is set to one poll, so ordinary
 barriers give up: every block returns, the call reports SSA_E_TIMEOUT, and the
 same CUDA context then gives the oracle's answer once the default bound is
 back.  Nothing waits forever and no access changes: the kernel only returns
@@ -32,6 +34,7 @@ def test_greedy_barrier_wait_gives_up_and_context_survives(orc):
         P.ssa_set_wait_polls(-1)
     assert e.value.status == SSA_E_ARG
     try:
+        P.ssa_set_greedy_mode(1)
         P.ssa_set_wait_polls(1)
         for _ in range(2):
             with pytest.raises(P.SSAError) as e:
@@ -42,6 +45,7 @@ def test_greedy_barrier_wait_gives_up_and_context_survives(orc):
         assert e.value.status == SSA_E_TIMEOUT
     finally:
         P.ssa_set_wait_polls(0)
+        P.ssa_set_greedy_mode(0)
     # the same context, default bound: the oracle's seeds and gains
     seeds, gains, cov = pool.max_coverage(20000, 50)
     og = orc.Graph.from_edges(el, orc.W_WC)
