@@ -135,7 +135,8 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
  * best values depend on the graph (wide bimodal sets favour mid_cap 0; deep
  * chains favour 16384; hubs of millions of in-edges favour an early hand-over).
  * ssa_autotune times a pilot batch of pilot_samples sets (0 = 8192) under the
- * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never}, after one
+ * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never} (and the
+ * global-bitmap warp tier of ssa_set_warp_tier where it exists), after one
  * untimed pass that sizes the pilot pool, and keeps the fastest in the graph
  * handle; an IC solve on an untuned graph first tunes it on 4096 sets.
  * ssa_set_tuning fixes both by hand (0 <= mid_cap <= 16384, heavy_groups >= 1;
@@ -150,13 +151,24 @@ ssa_status ssa_set_tuning(const ssa_graph* g, int32_t mid_cap, int32_t heavy_gro
  * default min(n, 2^20).  Applies to sampler scratch created afterwards (new
  * pools and solvers); results never depend on it.  SSA_E_ARG if negative. */
 ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue);
+/* Weighted-cascade IC on graphs whose n-bit bitmap does not fit shared memory
+ * (n/8 above 192 KB): with global_bitmap = 1 every sample is built by one warp
+ * whose visited set is its own n-bit bitmap in global memory and whose queue
+ * holds up to 2^16 nodes; long in-lists are walked by the whole warp, and
+ * larger sets, or samples that meet an in-list of more than heavy_groups
+ * (ssa_set_tuning) groups, go to the CTA tier.  0 (the default) keeps the
+ * shared-memory warp tiers of ssa_set_tuning.  ssa_autotune times this tier
+ * (with heavy_groups never and 4096) where it exists.  Results never depend
+ * on it. */
+ssa_status ssa_set_warp_tier(const ssa_graph* g, int32_t global_bitmap);
 
 /* Process-wide choice of the greedy kernel's launch shape (results never
- * depend on it): 0 (default) runs all picks of a Max-Coverage over at most 2^26
- * pool entries in one thread-block cluster of 16 (or 8) blocks, synchronised by
- * the hardware cluster barrier, and larger pools in a cooperative grid of one
- * block per SM; 1 always uses the cooperative grid; 2 always a cluster.  Applies
- * to launches after the call.  SSA_E_ARG for other values. */
+ * depend on it): 0 (default) uses one thread-block cluster of 16 (or 8) blocks,
+ * synchronised by the hardware cluster barrier, for solvers marked shared
+ * (ssa_solver_set_shared) on pools of at most 2^26 entries, and a cooperative
+ * grid of one block per SM otherwise; 1 always uses the cooperative grid; 2
+ * always a cluster.  Applies to launches after the call.  SSA_E_ARG for other
+ * values. */
 ssa_status ssa_set_greedy_mode(int32_t mode);
 
 /* Process-wide bound on the polls of each device-side wait: the grid barriers
@@ -259,6 +271,13 @@ ssa_status ssa_solver_solve(ssa_solver* s, const ssa_params* p, ssa_result* out)
  * Results do not depend on this setting.  Solves that time kernel classes
  * (ssa_result.want_kstats) launch separately. */
 ssa_status ssa_solver_set_graphs(ssa_solver* s, int32_t on);
+/* Mark the solver as sharing the GPU with concurrent solves (on = 1; the
+ * server sets it for its slots).  Its Max-Coverage over pools of up to 2^26
+ * entries then runs in one thread-block cluster of 16 SMs, leaving the rest of
+ * the GPU to the other solves, instead of a cooperative grid of one block per
+ * SM, which is faster for a solve alone on the GPU (the default, 0).  Results
+ * do not depend on this setting (see also ssa_set_greedy_mode). */
+ssa_status ssa_solver_set_shared(ssa_solver* s, int32_t on);
 ssa_status ssa_solver_free(ssa_solver* s);
 
 /* ------------------------------------------------------------------------ */

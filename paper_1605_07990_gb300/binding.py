@@ -79,11 +79,13 @@ EXPORTS = {
     "ssa_set_wait_polls": (C.c_int, [C.c_int64]),
     "ssa_set_greedy_mode": (C.c_int, [C.c_int32]),
     "ssa_set_queue_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ssa_set_warp_tier": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "ssa_solver_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_free": (C.c_int, [C.c_void_p]),
     "ssa_solver_set_graphs": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ssa_solver_set_shared": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_pool_create": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_void_p,
                                   C.POINTER(C.c_void_p)]),
     "ssa_pool_free": (C.c_int, [C.c_void_p]),
@@ -219,6 +221,10 @@ def ssa_set_tuning(g: Graph, mid_cap, heavy_groups=0x7FFFFFFF):
     _check(lib().ssa_set_tuning(g.h, int(mid_cap), int(heavy_groups)))
 
 
+def ssa_set_warp_tier(g: Graph, global_bitmap=0):
+    _check(lib().ssa_set_warp_tier(g.h, int(global_bitmap)))
+
+
 def ssa_set_queue_tuning(g: Graph, small_queue=0):
     _check(lib().ssa_set_queue_tuning(g.h, int(small_queue)))
 
@@ -316,6 +322,11 @@ class Solver:
     def set_graphs(self, on=True):
         """Run each round's index, greedy and stare as one CUDA graph."""
         _check(lib().ssa_solver_set_graphs(self.h, int(bool(on))))
+        return self
+
+    def set_shared(self, on=True):
+        """Mark the solver as sharing the GPU with concurrent solves (cluster-shaped greedy)."""
+        _check(lib().ssa_solver_set_shared(self.h, int(bool(on))))
         return self
 
     def free(self):

@@ -110,6 +110,7 @@ struct ssa_graph {
   mutable int tuned_mid_cap = -1;
   mutable int tuned_heavy = 0x7FFFFFFF;
   mutable int tuned_small_qcap = 0;  // queue of the small CTAs (0: min(n, 2^20))
+  mutable int tuned_warp_global = 0;  // weighted-cascade IC: the global-bitmap warp tier takes every sample
   GraphView view() const {
     GraphView v;
     v.n = n;
@@ -272,6 +273,9 @@ struct Sampler {
   uint64_t wsum = 0;
   int lt_cumulative = 0;
   int wc_implicit = 0;
+  int warp_global = 0;  // weighted-cascade IC: the global-bitmap warp tier takes every sample
+  uint32_t* wg_bitmap = nullptr;
+  int32_t* wg_queue = nullptr;
   int mid_cap = 16384;  // IC: largest set the global warp tier keeps (0 = none)
   int heavy_groups = 0x7FFFFFFF;  // IC: warp tiers hand samples with longer in-lists to the CTA tier
   int64_t edge_visits = 0, node_visits = 0, samples = 0, hit_samples = 0;
@@ -303,6 +307,7 @@ struct Sampler {
         mid_cap = G->tuned_mid_cap;
         heavy_groups = G->tuned_heavy;
       }
+      warp_global = (G->tuned_warp_global && cfg.wg_blocks > 0) ? 1 : 0;
     }
     X.num_sms = cfg.num_sms;
     edge_visits = node_visits = samples = hit_samples = 0;
@@ -362,6 +367,13 @@ struct Sampler {
       TRY(dev_alloc(&mid_queue, warps * mid_queue_per_warp(), X.st));
       TRY(dev_alloc(&mid_slots, warps * mid_queue_per_warp(), X.st));
     }
+    if (cfg.wg_blocks > 0) {
+      // the global-bitmap warp tier: an n-bit bitmap and a queue per warp
+      const size_t wgw = wg_tier_warps(cfg);
+      TRY(dev_alloc(&wg_bitmap, (size_t)words * wgw, X.st));
+      CU(cudaMemsetAsync(wg_bitmap, 0, sizeof(uint32_t) * (size_t)words * wgw, X.st));
+      TRY(dev_alloc(&wg_queue, wg_queue_per_warp() * wgw, X.st));
+    }
     return SSA_OK;
   }
   void release(cudaStream_t st) {
@@ -373,6 +385,8 @@ struct Sampler {
     dev_free(mid_hash, st);
     dev_free(mid_queue, st);
     dev_free(mid_slots, st);
+    dev_free(wg_bitmap, st);
+    dev_free(wg_queue, st);
     dev_free(fail_list, st);
     dev_free(redo_list, st);
     dev_free(slot_bitmap, st);
@@ -391,6 +405,9 @@ struct Sampler {
     J.model = model;
     J.lt_cumulative = lt_cumulative;
     J.wc_implicit = wc_implicit;
+    J.warp_global = warp_global;
+    J.wg_bitmap = wg_bitmap;
+    J.wg_queue = wg_queue;
     J.seed = seed;
     J.stream = stream;
     J.j0 = j0;
@@ -636,6 +653,7 @@ struct Cover {
   unsigned int* h_sync = nullptr;        // 128 words
   unsigned long long* h_count = nullptr;
   int64_t total_e = 0;                   // entries of the sets the next greedy covers (greedy_prepare)
+  bool shared_gpu = false;               // the solve shares the GPU with others (greedy launch shape)
 
   ssa_status init(int64_t nn, Exec& X) {
     n = nn;
@@ -854,7 +872,7 @@ struct Cover {
     J.cache_n = hist + 2 * 4096;
     J.wait_polls = greedy_wait_polls();
     int blocks = 0;
-    CU(launch_greedy(J, X.st, X.num_sms, &blocks));
+    CU(launch_greedy(J, X.st, X.num_sms, &blocks, shared_gpu));
     X.end(h);
     X.launches += 1;
     CU(cudaMemcpyAsync(h_seeds, d_seeds, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, X.st));
@@ -987,10 +1005,12 @@ ssa_status estimate_inf_dev(Sampler& S, Cover& C, uint64_t seed, uint32_t stream
 // tier and the CTA tier, and keep the fastest for this graph.  The candidates
 // give identical sets (keyed randomness); only the time differs.
 ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, double* ms_out) {
-  // (mid_cap, heavy in-list hand-over in 4-edge groups; 0x7FFFFFFF = never)
-  const int cands[4][2] = {{0, 0x7FFFFFFF}, {mid_tier_max_cap(), 0x7FFFFFFF}, {0, 4096}, {mid_tier_max_cap(), 4096}};
+  // (mid_cap, heavy in-list hand-over in 4-edge groups; 0x7FFFFFFF = never; global-bitmap
+  // warp tier for every sample), the last only where the graph has that tier
+  const int cands[6][3] = {{0, 0x7FFFFFFF, 0}, {mid_tier_max_cap(), 0x7FFFFFFF, 0}, {0, 4096, 0},
+                           {mid_tier_max_cap(), 4096, 0}, {0, 0x7FFFFFFF, 1}, {0, 4096, 1}};
   double best_ms = 1e300;
-  int best = cands[1][0], best_heavy = cands[1][1];
+  int best = cands[1][0], best_heavy = cands[1][1], best_global = 0;
   // One sampler and one pool serve every candidate: the tier settings are
   // plain fields, and the pool keeps the capacity that an untimed first pass
   // grew, so each timed pass samples the same pilot sets without re-runs.
@@ -1000,10 +1020,12 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
   ssa_status st = S.init(G, 0, nullptr, X);
   if (st == SSA_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
     st = fail(SSA_E_CUDA, "autotune: cudaEventCreate failed");
-  for (int c = -1; c < 4 && st == SSA_OK; ++c) {
+  const int ncand = S.cfg.wg_blocks > 0 ? 6 : 4;
+  for (int c = -1; c < ncand && st == SSA_OK; ++c) {
     const auto& cand = cands[c < 0 ? 0 : c];
     S.mid_cap = cand[0];
     S.heavy_groups = cand[1];
+    S.warp_global = cand[2];
     P.count = 0;
     P.entries = 0;
     P.bounds.assign(1, {0, 0});
@@ -1020,6 +1042,7 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
       best_ms = ms;
       best = cand[0];
       best_heavy = cand[1];
+      best_global = cand[2];
     }
   }
   if (a) cudaEventDestroy(a);
@@ -1032,6 +1055,7 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
     std::lock_guard<std::mutex> lock(G->tune_mu);
     G->tuned_mid_cap = best;
     G->tuned_heavy = best_heavy;
+    G->tuned_warp_global = best_global;
   }
   if (chosen) *chosen = best;
   if (ms_out) *ms_out = best_ms;
@@ -1095,6 +1119,7 @@ struct ssa_solver {
   // CUDA graphs of a round's device work (index, greedy, stare), one
   // executable per (algorithm, round), patched in place by later solves
   bool use_graphs = false;
+  bool shared_gpu = false;  // concurrent solves share the GPU (serving): cluster-shaped greedy
   std::vector<cudaGraphExec_t> gexec;
   int64_t graph_launches = 0;
 
@@ -1245,6 +1270,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     } else if ((st = C.reset(X)) != SSA_OK) {
       break;
     }
+    C.shared_gpu = sv->shared_gpu;
     const double scale = p->benefit ? (double)S.wsum : (double)n;
     const int64_t base = (int64_t)std::ceil(P.lambda);
     for (;;) {
@@ -1586,6 +1612,13 @@ ssa_status ssa_autotune(const ssa_graph* g, ssa_model model, int64_t pilot_sampl
   return SSA_OK;
 }
 
+ssa_status ssa_set_warp_tier(const ssa_graph* g, int32_t global_bitmap) {
+  if (!g) return fail(SSA_E_ARG, "null graph");
+  std::lock_guard<std::mutex> lock(g->tune_mu);
+  g->tuned_warp_global = global_bitmap != 0 ? 1 : 0;
+  return SSA_OK;
+}
+
 ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue) {
   if (!g || small_queue < 0) return fail(SSA_E_ARG, "need a graph and small_queue >= 0");
   std::lock_guard<std::mutex> lock(g->tune_mu);
@@ -1647,6 +1680,12 @@ ssa_status ssa_solver_solve(ssa_solver* s, const ssa_params* p, ssa_result* out)
 ssa_status ssa_solver_set_graphs(ssa_solver* s, int32_t on) {
   if (!s) return fail(SSA_E_ARG, "null solver");
   s->use_graphs = on != 0;
+  return SSA_OK;
+}
+
+ssa_status ssa_solver_set_shared(ssa_solver* s, int32_t on) {
+  if (!s) return fail(SSA_E_ARG, "null solver");
+  s->shared_gpu = on != 0;
   return SSA_OK;
 }
 

@@ -817,14 +817,16 @@ std::atomic<int> g_greedy_mode{0};
 
 void set_greedy_mode(int mode) { g_greedy_mode.store(mode); }
 
-cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used) {
-  // Pools of up to GREEDY_CLUSTER_ENTRIES entries: all picks in one thread-block
-  // cluster (hardware cluster barriers, a fraction of a microsecond); larger
-  // pools, whose first picks decrement millions of gains, use one 1024-thread
-  // block per SM in a cooperative launch.
+cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used, bool shared_gpu) {
+  // A solve that shares the GPU with others (serving) runs all picks of a pool
+  // of up to GREEDY_CLUSTER_ENTRIES entries in one thread-block cluster: 16 SMs,
+  // hardware cluster barriers, and the rest of the GPU free for the other
+  // solves.  Otherwise (and for larger pools, whose first picks decrement
+  // millions of gains) one 1024-thread block per SM in a cooperative launch,
+  // the faster shape for a solve that has the GPU to itself.
   const int mode = g_greedy_mode.load();
   const int csize = mode == 1 ? 0 : greedy_cluster_size();
-  if (csize > 0 && (mode == 2 || J.total_entries <= GREEDY_CLUSTER_ENTRIES)) {
+  if (csize > 0 && (mode == 2 || (shared_gpu && J.total_entries <= GREEDY_CLUSTER_ENTRIES))) {
     *blocks_used = csize;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(csize);

@@ -48,6 +48,9 @@ struct SampleJob {
   int lt_cumulative = 0;         // LT with explicit in-weights: pick by running threshold sums
   int wc_implicit = 0;           // IC with weighted-cascade weights: thresholds from in-degrees,
                                  // records read for live edges only
+  int warp_global = 0;           // weighted-cascade IC: every sample through the global-bitmap warp tier
+  uint32_t* wg_bitmap = nullptr; // that tier: per warp bitmap_words words, zero between samples
+  int32_t* wg_queue = nullptr;   // that tier: per warp wg_queue_per_warp() entries
   uint64_t seed = 0;
   uint32_t stream = 0;
   int64_t j0 = 0, count = 0;     // samples [j0, j0+count), or work_list[0, count)
@@ -95,6 +98,7 @@ struct LaunchCfg {
   int cta_threads = 1024;
   int small_blocks = 0;  // small CTAs (256 threads) when the bitmap lives in global memory
   int small_qcap = 0;
+  int wg_blocks = 0;     // global-bitmap warp tier (0: not available for this graph)
   bool cta_smem_bitmap = false;
   int64_t smem_bitmap_bytes = 0;
 };
@@ -119,6 +123,8 @@ cudaError_t rmat_graph(int scale, int64_t m_draw, uint32_t ta, uint32_t tab, uin
 LaunchCfg sampler_config(const GraphView& g, int model, bool wc_implicit);
 size_t sampler_scratch_bytes(const GraphView& g, const LaunchCfg& c);
 size_t mid_tier_words(const LaunchCfg& c);  // number of warps of the global-memory tier
+size_t wg_tier_warps(const LaunchCfg& c);   // warps of the global-bitmap tier
+size_t wg_queue_per_warp();
 int mid_tier_max_cap();
 size_t mid_hash_per_warp();
 size_t mid_queue_per_warp();
@@ -172,11 +178,12 @@ struct GreedyJob {
 constexpr long long GREEDY_DEFAULT_WAIT_POLLS = 1ll << 22;  // about a second with the poll back-off
 // Process-wide poll limit of the greedy kernel's grid-barrier waits (ssa_set_wait_polls).
 long long greedy_wait_polls();
-// All k picks in one launch: one thread-block cluster for pools of up to
-// GREEDY_CLUSTER_ENTRIES entries, else a cooperative grid (bounded grid barriers).
+// All k picks in one launch: a cooperative grid (bounded grid barriers), or,
+// for a solve that shares the GPU with others and a pool of up to
+// GREEDY_CLUSTER_ENTRIES entries, one thread-block cluster.
 constexpr unsigned long long GREEDY_CLUSTER_ENTRIES = 1ull << 26;
-cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used);
-// 0: by pool size (default); 1: always the cooperative grid; 2: always a cluster (when the device has one)
+cudaError_t launch_greedy(const GreedyJob& J, cudaStream_t st, int num_sms, int* blocks_used, bool shared_gpu);
+// 0: by the rule above (default); 1: always the cooperative grid; 2: always a cluster (when the device has one)
 void set_greedy_mode(int mode);
 cudaError_t launch_add_counts(int32_t* total, const int32_t* add, int64_t n, cudaStream_t st, int num_sms);
 // SASS and PTX versions (major*10 + minor) of the device code the CUDA runtime loaded for this library

@@ -415,7 +415,7 @@ __device__ __forceinline__ void warp_store_set(const SampleJob& J, int64_t j, co
 }
 
 template <int MODE, int TIER, bool WC>
-__global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
+__global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J) {
   constexpr int HBITS = Tier<TIER>::HBITS, QCAP = Tier<TIER>::QCAP;
   __shared__ __align__(16) uint32_t s_hash[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_HASH : 4];
   __shared__ int32_t s_q[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_QCAP : 4];
@@ -520,6 +520,92 @@ __global__ void __launch_bounds__(WT_WARPS * 32) k_sample_warp_ic(SampleJob J) {
       // clear only the slots this sample used (tail <= QCAP + 32 entries recorded)
       for (int i = lane; i < tail; i += 32) H[slots[i]] = 0u;
     }
+    __syncwarp();
+  }
+  flush_stats(J.ctr, ev, nv, dr, lane, false);
+}
+
+// Weighted-cascade IC, one warp per sample of up to GQ_CAP nodes, with the
+// visited set as a per-warp n-bit bitmap in global memory and the BFS queue in
+// global memory.  Under weighted cascade a visited node costs one atomicOr
+// against the thousands of coins of a typical in-list, so one tier serves
+// every set size without a hand-over: long in-lists are walked by the whole
+// warp (wc_walk), and only sets that outgrow the queue go to the CTA tier.
+constexpr int GQ_CAP = 1 << 16;
+constexpr int GQ_SLOTS = GQ_CAP + 32;  // room for one round past the cap
+
+template <int MODE>
+__global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob J) {
+  __shared__ uint32_t s_stage[WT_WARPS][STAGE];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const size_t gwarp = (size_t)blockIdx.x * WT_WARPS + wid;
+  uint32_t* bits = J.wg_bitmap + gwarp * (size_t)J.bitmap_words;
+  int32_t* Q = J.wg_queue + gwarp * (size_t)GQ_SLOTS;
+  unsigned long long ev = 0, nv = 0, dr = 0;
+  for (;;) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
+    idx = __shfl_sync(FULL_MASK, idx, 0);
+    if (idx >= (unsigned long long)J.count) break;
+    const int64_t j = sample_at(J, idx);
+    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
+    const int32_t root = pick_root(J, j);
+    if (lane == 0) {
+      atomicOr(bits + (root >> 5), 1u << (root & 31));
+      Q[0] = root;
+    }
+    int tail = 1, head = 0;
+    bool overflow = false;
+    bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
+    __syncwarp();
+    auto known = [](uint32_t) { return false; };
+    auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
+      bool is_new = false;
+      if (u != NO_NODE) {
+        const uint32_t mask = 1u << (u & 31);
+        is_new = !(atomicOr(bits + (u >> 5), mask) & mask);
+      }
+      const unsigned m = __ballot_sync(FULL_MASK, is_new);
+      bool h = false;
+      if (is_new) {
+        Q[tail + __popc(m & lt_mask)] = (int32_t)u;  // tail <= GQ_CAP before this round: fits GQ_SLOTS
+        if (MODE == MODE_HIT) h = test_bit(J.seed_bits, u);
+      }
+      tail += __popc(m);
+      if (MODE == MODE_HIT) hit = __any_sync(FULL_MASK, h) || hit;
+      if (tail > GQ_CAP) overflow = true;
+      return overflow || hit;
+    };
+    // an in-list of more than warp_heavy_groups groups (a hub) hands the sample to the CTA tier,
+    // whose warps split long lists between them
+    auto to_cta = [](int32_t, uint32_t, uint32_t, int) { return HEAVY_ABORT; };
+    bool handoff = false;
+    while (head < tail && !overflow && !hit) {
+      const int cnt = min(32, tail - head);
+      __syncwarp();
+      const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
+      __syncwarp();
+      if (expand_ic<true>(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
+          2) {
+        handoff = true;
+        break;
+      }
+      head += cnt;
+    }
+    __syncwarp();
+    if (overflow || handoff) {
+      if (lane == 0) {
+        const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
+        J.big_list[b] = j;
+      }
+    } else {
+      if (MODE == MODE_STORE) warp_store_set(J, j, Q, tail, lane);
+      else if (lane == 0) J.hit[j - J.j0] = hit ? 1 : 0;
+      if (lane == 0) nv += (unsigned long long)tail;
+    }
+    __syncwarp();
+    // clear the words of this sample's nodes (every set bit has its queue entry)
+    for (int i = lane; i < tail; i += 32) bits[Q[i] >> 5] = 0u;
     __syncwarp();
   }
   flush_stats(J.ctr, ev, nv, dr, lane, false);
@@ -1021,10 +1107,19 @@ LaunchCfg sampler_config(const GraphView& g, int model, bool wc) {
     c.cta_blocks = std::max(8, c.num_sms / 4);
   }
   c.mid_blocks = c.num_sms * 2;  // 16 warps per SM, each with its own global hash and queue
+  // global-bitmap warp tier (weighted-cascade IC, bitmap in global memory): 32
+  // warps per SM, each with an n-bit bitmap and a GQ_SLOTS queue, or 16 where
+  // the bitmaps would pass 24 GB
+  if (model == 0 && wc && !c.cta_smem_bitmap) {
+    const double per_block = (double)words * 4.0 * WT_WARPS;
+    c.wg_blocks = c.num_sms * ((double)c.num_sms * 4 * per_block <= 24e9 ? 4 : 2);
+  }
   return c;
 }
 
 size_t mid_tier_words(const LaunchCfg& c) { return (size_t)c.mid_blocks * WT_WARPS; }
+size_t wg_tier_warps(const LaunchCfg& c) { return (size_t)c.wg_blocks * WT_WARPS; }
+size_t wg_queue_per_warp() { return GQ_SLOTS; }
 int mid_tier_max_cap() { return Tier<1>::QCAP; }
 size_t mid_hash_per_warp() { return MID_HASH; }
 size_t mid_queue_per_warp() { return MID_QSLOTS; }
@@ -1044,7 +1139,10 @@ static void launch_warp_ic(const SampleJob& J, const LaunchCfg& c, cudaStream_t 
 
 cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
   const dim3 grid(c.warp_blocks), block(WT_WARPS * 32);
-  if (J.model == 0) {
+  if (J.model == 0 && J.wc_implicit && J.warp_global && c.wg_blocks > 0) {
+    if (J.mode == MODE_STORE) k_sample_warp_wcg<MODE_STORE><<<c.wg_blocks, block, 0, st>>>(J);
+    else k_sample_warp_wcg<MODE_HIT><<<c.wg_blocks, block, 0, st>>>(J);
+  } else if (J.model == 0) {
     if (J.mode == MODE_STORE) {
       if (J.wc_implicit) launch_warp_ic<MODE_STORE, true>(J, c, st);
       else launch_warp_ic<MODE_STORE, false>(J, c, st);

@@ -127,8 +127,10 @@ struct ssa_server {
       ssa_status s = SSA_OK;
       if (!solvers[(size_t)r->graph]) {
         s = ssa_solver_create(graphs[(size_t)r->graph], st, 0, &solvers[(size_t)r->graph]);
-        // each round's index, greedy and stare as one CUDA graph, reused by later requests
+        // each round's index, greedy and stare as one CUDA graph, reused by later requests;
+        // the greedy in one thread-block cluster, so concurrent requests keep the other SMs
         if (s == SSA_OK) s = ssa_solver_set_graphs(solvers[(size_t)r->graph], 1);
+        if (s == SSA_OK) s = ssa_solver_set_shared(solvers[(size_t)r->graph], 1);
       }
       if (s == SSA_OK) {
         r->seeds.assign((size_t)r->p.k, -1);
