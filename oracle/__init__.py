@@ -60,6 +60,7 @@ def _load():
     vp, i64, u64, i32, u32, dbl = C.c_void_p, C.c_int64, C.c_uint64, C.c_int32, C.c_uint32, C.c_double
     sig = {
         "orc_philox4x32_10": (None, [vp, vp, vp]),
+        "orc_wc_gap": (u32, [i64, u64]),
         "orc_graph_build": (vp, [i64, i64, vp, vp, C.c_int, vp, u64]),
         "orc_graph_free": (None, [vp]),
         "orc_graph_off": (vp, [vp]), "orc_graph_src": (vp, [vp]), "orc_graph_thr": (vp, [vp]),
@@ -87,6 +88,12 @@ def _load():
         f.argtypes = args
     _lib = L
     return L
+
+
+def wc_gap(d: int, U: int) -> int:
+    """Dead-edge run before the next live one in a weighted-cascade in-list of
+    d edges, for the 64-bit uniform U (the gap form of oracle.c)."""
+    return int(_load().orc_wc_gap(d, U & 0xFFFFFFFFFFFFFFFF))
 
 
 def _p(a):

@@ -17,8 +17,10 @@
  *     threshold; 0xFFFFFFFF means probability exactly 1.
  *   - RR set (Definition 2): random source v, random sample graph g, the nodes
  *     that reach v in g.  IC (Sec. 2.1): each edge is live independently with
- *     probability w.  LT (Sec. 2.1) in its live-edge form: each node keeps at
- *     most one in-edge, (u,v) with probability w(u,v).
+ *     probability w; under weighted-cascade weights the live in-edges of a
+ *     node are drawn as geometric gaps (the same law; see "gap form" below).
+ *     LT (Sec. 2.1) in its live-edge form: each node keeps at most one
+ *     in-edge, (u,v) with probability w(u,v).
  *   - WRIS (Sec. 6.3.1): the source is drawn proportionally to node benefit.
  *   - Cov_R(S) (Eq. 1); Max-Coverage (Algorithm 2); Estimate-Inf
  *     (Algorithm 3); SSA (Algorithm 1, default parameters Eq. "set_ep");
@@ -71,8 +73,9 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  *   key     = (lo32(seed), hi32(seed))
  *   counter = (lo32(x), hi32(x), lo32(j), purpose<<28 | stream<<20 | (j>>32 & 0xFFFFF))
  * purposes: ROOT=1 (x=0), IC=2 (x=e>>2, word e&3), LT=3 (x=v, word 0),
- *           WEIGHT=5 (x=e, j=0, stream=0).                                  */
-enum { P_ROOT = 1, P_IC = 2, P_LT = 3, P_WEIGHT = 5 };
+ *           SKIP=4 (x = v | (c>>1)<<32, words 2(c&1), 2(c&1)+1 as one 64-bit
+ *           uniform for gap c of node v's in-list), WEIGHT=5 (x=e, j=0, stream=0). */
+enum { P_ROOT = 1, P_IC = 2, P_LT = 3, P_SKIP = 4, P_WEIGHT = 5 };
 
 static void keyed(uint64_t seed, uint32_t purpose, uint32_t stream, uint64_t j, uint64_t x,
                   uint32_t out[4]) {
@@ -165,6 +168,58 @@ int64_t orc_graph_n(const orc_graph* g) { return g->n; }
 int64_t orc_graph_m(const orc_graph* g) { return g->m; }
 
 /* ------------------------------------------------------------------------ */
+/* Weighted cascade in gap form.  Under IC every in-edge of v is live on its  */
+/* own coin; with weighted-cascade weights all d = d_in(v) >= 2 of them have   */
+/* the same probability p = t/2^32, t = floor(2^32/d), so the live edges of    */
+/* v's in-list can be found by drawing the run G of dead edges before each     */
+/* live one: P(G >= g) = q^g with q = 1 - p (a geometric law).  That is the    */
+/* same law as d independent coins, at a cost in the number of live edges      */
+/* rather than in d.  (d = 1: the one edge has probability 1, no draw.)        */
+/*                                                                           */
+/* Arithmetic, integers only so that every platform gets the same gaps:       */
+/*   numbers in [0,1) are Q64 (x -> floor(x 2^64)), products truncate:         */
+/*   mulq(a,b) = floor(a b / 2^64);  q = (2^32 - t) << 32 exactly;             */
+/*   P_0 = q, P_(i+1) = mulq(P_i, P_i)  (q^(2^i));  J = bit length of d;        */
+/*   G(U) = the g in [0, 2^J) found by testing bits J-1 .. 0 in turn: bit i   */
+/*   is set when U < mulq(A, P_i), A the product taken so far (P_i itself     */
+/*   at the first set bit), which then becomes A.                              */
+/* G(U) is the largest g with U < q^g, up to the truncation (relative error   */
+/* below 2^-50 at every threshold; pinned against exact powers in the tests). */
+/* The walk: pos = 0, gap c = 0, 1, ...: G = G(U_c); stop when G >= d - pos;  */
+/* else edge off[v] + pos + G is live and pos moves past it.                   */
+/* ------------------------------------------------------------------------ */
+static uint64_t mulq(uint64_t a, uint64_t b) {
+  return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+uint32_t orc_wc_gap(int64_t d, uint64_t U) {
+  if (d < 2 || d > 0x7FFFFFFF) return 0;
+  uint32_t t = (uint32_t)((UINT64_C(1) << 32) / (uint64_t)d);
+  uint64_t q = ((UINT64_C(1) << 32) - t) << 32;
+  int J = 0;
+  while ((INT64_C(1) << J) <= d) ++J;  /* 2^J > d */
+  uint64_t P[32];
+  P[0] = q;
+  for (int i = 1; i < J; ++i) P[i] = mulq(P[i - 1], P[i - 1]);
+  uint64_t A = 0;
+  int first = 1;
+  uint32_t g = 0;
+  for (int i = J - 1; i >= 0; --i) {
+    uint64_t cand = first ? P[i] : mulq(A, P[i]);
+    if (U < cand) { A = cand; first = 0; g |= UINT32_C(1) << i; }
+  }
+  return g;
+}
+
+/* the 64-bit uniform of gap c of node v in sample j */
+static uint64_t skip_uniform(uint64_t seed, uint32_t stream, uint64_t j, int32_t v, uint64_t c) {
+  uint32_t r[4];
+  keyed(seed, P_SKIP, stream, j, (uint64_t)(uint32_t)v | ((c >> 1) << 32), r);
+  unsigned w = 2u * (unsigned)(c & 1u);
+  return (uint64_t)r[w] | ((uint64_t)r[w + 1] << 32);
+}
+
+/* ------------------------------------------------------------------------ */
 /* RR sets (Definition 2).                                                   */
 /* ------------------------------------------------------------------------ */
 enum { MODEL_IC = 0, MODEL_LT = 1 };
@@ -222,7 +277,31 @@ static int64_t rr_set(orc_sampler* s, uint32_t stream, uint64_t j, int32_t* out)
   int64_t size = 0;
   s->queue[size++] = root;
   s->visited[root] = 1;
-  if (s->model == MODEL_IC) {
+  if (s->model == MODEL_IC && g->weighting == W_WC) {
+    /* reverse BFS; the live in-edges of each node by the gap walk above */
+    for (int64_t head = 0; head < size; ++head) {
+      int32_t v = s->queue[head];
+      int64_t lo = g->off[v], d = g->off[v + 1] - lo;
+      s->edge_visits += d;
+      int64_t pos = 0;
+      for (uint64_t c = 0; pos < d; ++c) {
+        int64_t e;
+        if (d == 1) {
+          e = lo;
+          pos = 1;
+        } else {
+          uint32_t G = orc_wc_gap(d, skip_uniform(s->seed, stream, j, v, c));
+          if ((int64_t)G >= d - pos) break;
+          e = lo + pos + G;
+          pos += (int64_t)G + 1;
+        }
+        if (!s->visited[g->src[e]]) {
+          s->visited[g->src[e]] = 1;
+          s->queue[size++] = g->src[e];
+        }
+      }
+    }
+  } else if (s->model == MODEL_IC) {
     /* reverse BFS over live in-edges: edge e is live in sample j iff its
      * keyed draw is below thr[e] */
     for (int64_t head = 0; head < size; ++head) {
