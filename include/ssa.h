@@ -23,8 +23,19 @@
  *       key     = (lo32(seed), hi32(seed))
  *       counter = (lo32(x), hi32(x), lo32(j), purpose<<28 | stream<<20 | (j>>32 & 0xFFFFF))
  *       purposes ROOT=1 (x=0), IC=2 (x=e>>2, output word e&3), LT=3 (x=v, word 0),
- *                WEIGHT=5 (x=e, j=0, stream=0)
+ *                SKIP=4 (x = v | (c>>1)<<32, words 2(c&1), 2(c&1)+1 as one 64-bit
+ *                uniform U for gap c of v's in-list), WEIGHT=5 (x=e, j=0, stream=0)
  *     where j is the sample id, e the CSR position of an in-edge and v a node.
+ *     IC under SSA_W_WC draws no per-edge coins: all d = d_in(v) >= 2
+ *     in-edges of v have probability p = t/2^32 (t below), so the run G of
+ *     dead edges before each live one is geometric, P(G >= g) = q^g, q = 1-p
+ *     (the law of d independent coins).  In Q64 integers (products truncated
+ *     to their high 64 bits): Q = (2^32 - t) << 32, P_0 = Q, P_(i+1) = P_i^2;
+ *     G(U) tests bits J-1 .. 0 (J = bit length of d), setting bit i when
+ *     U < A * P_i with A the product taken so far (P_i alone at the first).
+ *     From pos = 0, gap c gives the live edge off[v] + pos + G, after which
+ *     pos moves past it; the walk ends when G >= d - pos.  d = 1: the one
+ *     edge is live without a draw.
  */
 #ifndef SSA_H
 #define SSA_H
@@ -135,10 +146,12 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
  * best values depend on the graph (wide bimodal sets favour mid_cap 0; deep
  * chains favour 16384; hubs of millions of in-edges favour an early hand-over).
  * ssa_autotune times a pilot batch of pilot_samples sets (0 = 8192) under the
- * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never} (and the
- * global-bitmap warp tier of ssa_set_warp_tier where it exists), after one
+ * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never}, after one
  * untimed pass that sizes the pilot pool, and keeps the fastest in the graph
- * handle; an IC solve on an untuned graph first tunes it on 4096 sets.
+ * handle; an IC solve on an untuned graph first tunes it on 4096 sets.  Under
+ * SSA_W_WC the in-lists are walked by gaps and none is heavy: the candidates
+ * are mid_cap in {0, 16384} and the global-bitmap warp tier of
+ * ssa_set_warp_tier where it exists.
  * ssa_set_tuning fixes both by hand (0 <= mid_cap <= 16384, heavy_groups >= 1;
  * 0x7FFFFFFF = never hand over).  Results never depend on the tuning.  For
  * SSA_LT ssa_autotune has nothing to tune. */
@@ -154,12 +167,9 @@ ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue);
 /* Weighted-cascade IC on graphs whose n-bit bitmap does not fit shared memory
  * (n/8 above 192 KB): with global_bitmap = 1 every sample is built by one warp
  * whose visited set is its own n-bit bitmap in global memory and whose queue
- * holds up to 2^16 nodes; long in-lists are walked by the whole warp, and
- * larger sets, or samples that meet an in-list of more than heavy_groups
- * (ssa_set_tuning) groups, go to the CTA tier.  0 (the default) keeps the
- * shared-memory warp tiers of ssa_set_tuning.  ssa_autotune times this tier
- * (with heavy_groups never and 4096) where it exists.  Results never depend
- * on it. */
+ * holds up to 2^16 nodes; larger sets go to the CTA tier.  0 (the default)
+ * keeps the hash warp tiers of ssa_set_tuning.  ssa_autotune times this tier
+ * where it exists.  Results never depend on it. */
 ssa_status ssa_set_warp_tier(const ssa_graph* g, int32_t global_bitmap);
 
 /* Process-wide choice of the greedy kernel's launch shape (results never

@@ -1006,9 +1006,13 @@ ssa_status estimate_inf_dev(Sampler& S, Cover& C, uint64_t seed, uint32_t stream
 // give identical sets (keyed randomness); only the time differs.
 ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, double* ms_out) {
   // (mid_cap, heavy in-list hand-over in 4-edge groups; 0x7FFFFFFF = never; global-bitmap
-  // warp tier for every sample), the last only where the graph has that tier
-  const int cands[6][3] = {{0, 0x7FFFFFFF, 0}, {mid_tier_max_cap(), 0x7FFFFFFF, 0}, {0, 4096, 0},
-                           {mid_tier_max_cap(), 4096, 0}, {0, 0x7FFFFFFF, 1}, {0, 4096, 1}};
+  // warp tier for every sample).  Weighted cascade walks in-lists by gaps, so no list is
+  // heavy: its candidates are the hash tiers and, where the graph has it, the bitmap tier.
+  const int cands_thr[4][3] = {{0, 0x7FFFFFFF, 0}, {mid_tier_max_cap(), 0x7FFFFFFF, 0}, {0, 4096, 0},
+                               {mid_tier_max_cap(), 4096, 0}};
+  const int cands_wc[3][3] = {{0, 0x7FFFFFFF, 0}, {mid_tier_max_cap(), 0x7FFFFFFF, 0}, {0, 0x7FFFFFFF, 1}};
+  const bool wc = G->weighting == SSA_W_WC;
+  const int(*cands)[3] = wc ? cands_wc : cands_thr;
   double best_ms = 1e300;
   int best = cands[1][0], best_heavy = cands[1][1], best_global = 0;
   // One sampler and one pool serve every candidate: the tier settings are
@@ -1020,7 +1024,7 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
   ssa_status st = S.init(G, 0, nullptr, X);
   if (st == SSA_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
     st = fail(SSA_E_CUDA, "autotune: cudaEventCreate failed");
-  const int ncand = S.cfg.wg_blocks > 0 ? 6 : 4;
+  const int ncand = wc ? (S.cfg.wg_blocks > 0 ? 3 : 2) : 4;
   for (int c = -1; c < ncand && st == SSA_OK; ++c) {
     const auto& cand = cands[c < 0 ? 0 : c];
     S.mid_cap = cand[0];

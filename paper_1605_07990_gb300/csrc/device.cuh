@@ -11,7 +11,7 @@ namespace ssa {
 constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr uint32_t NO_NODE = 0xffffffffu;
 
-enum : uint32_t { PURPOSE_ROOT = 1, PURPOSE_IC = 2, PURPOSE_LT = 3, PURPOSE_WEIGHT = 5 };
+enum : uint32_t { PURPOSE_ROOT = 1, PURPOSE_IC = 2, PURPOSE_LT = 3, PURPOSE_SKIP = 4, PURPOSE_WEIGHT = 5 };
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box
 // (two 32x32->64 products, the high halves xored into the other words), the

@@ -1,20 +1,23 @@
 // RR-set samplers (Definition 2) for IC and LT (Sec. 2.1) on sm_103a.
 //
-// Two tiers share one work list of sample ids:
-//   * warp tier: one warp per sample, visited set as an open-addressing hash
-//     in shared memory and the BFS queue beside it.  Sets that outgrow the
-//     queue are handed to the CTA tier (their partial work is dropped).
-//   * CTA tier: one CTA per sample, visited set as an n-bit bitmap (shared
-//     memory when it fits, else a per-CTA global slot), level-synchronous
-//     BFS with warps pulling 32-node batches from the current level.
-// IC frontier expansion is edge-balanced inside a warp: 32 frontier nodes'
-// in-edge ranges are cut into 4-edge groups (the unit of one Philox draw, one
-// aligned 32-byte sector of {src,thr} records) and the groups are dealt to
-// lanes by a warp prefix sum.  The kernel is bound by integer issue (Philox),
-// so the expansion (a) takes the Philox round keys from the kernel parameters,
-// (b) in the CTA tier skips the draw of a group whose live-able edges all
-// come from already-visited nodes (such an edge cannot change the set), and
-// (c) compacts the live candidates of a 128-edge slab into one insert round.
+// Tiers share one work list of sample ids:
+//   * warp tiers: one warp per sample, visited set as an open-addressing hash
+//     (shared memory, or global memory for mid-size sets) or, for weighted
+//     cascade, a per-warp n-bit bitmap in global memory; the BFS queue beside
+//     it.  Sets that outgrow the queue are handed on (their partial work is
+//     dropped).
+//   * CTA tier: one CTA per large sample, visited set as an n-bit bitmap
+//     (shared memory when it fits, else a per-CTA global slot).
+// IC with per-edge thresholds: frontier expansion is edge-balanced inside a
+// warp: 32 frontier nodes' in-edge ranges are cut into 4-edge groups (the
+// unit of one Philox draw, one aligned 32-byte sector of {src,thr} records)
+// dealt to lanes by a warp prefix sum; the CTA tier skips the draw of a group
+// whose edges all come from already-visited nodes and shares long in-lists
+// between its warps.
+// IC with weighted-cascade weights: every in-edge of a node has the same
+// probability, so each lane walks one frontier node's in-list by geometric
+// gaps between live edges (the gap form below); the work per node is a few
+// 64-bit products and one Philox draw per two gaps, whatever its in-degree.
 #include <algorithm>
 
 #include "device.cuh"
@@ -52,6 +55,19 @@ __device__ __forceinline__ SampleConst sample_const(const uint32_t* rk, uint32_t
 __device__ __forceinline__ uint4 philox_x(uint32_t x, const SampleConst& sc, const uint32_t* rk) {
   // round 1 with c.y = 0 and the sample constants folded in
   uint4 c = make_uint4(sc.s0, sc.s1, __umulhi(PHILOX_M0, x) ^ sc.s2, PHILOX_M0 * x);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t lo0 = PHILOX_M0 * c.x, hi0 = __umulhi(PHILOX_M0, c.x);
+    const uint32_t lo1 = PHILOX_M1 * c.z, hi1 = __umulhi(PHILOX_M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
+// Philox4x32-10 of the counter (x, y, jlo, cw): philox_x with a second
+// counter word y, which enters the first round beside the sample constants.
+__device__ __forceinline__ uint4 philox_xy(uint32_t x, uint32_t y, const SampleConst& sc, const uint32_t* rk) {
+  uint4 c = make_uint4(sc.s0 ^ y, sc.s1, __umulhi(PHILOX_M0, x) ^ sc.s2, PHILOX_M0 * x);
 #pragma unroll
   for (int r = 1; r < 10; ++r) {
     const uint32_t lo0 = PHILOX_M0 * c.x, hi0 = __umulhi(PHILOX_M0, c.x);
@@ -130,33 +146,12 @@ __device__ __forceinline__ bool deliver(uint32_t cand, uint32_t u0, uint32_t u1,
 // handed to visit(u) in rounds of 32 (NO_NODE for idle lanes).  known(u) may
 // report tails already in the set so their edges need no draw.  Returns the
 // warp-uniform "stop" of visit.
-template <bool WC, class Known, class Visit>
+template <class Known, class Visit>
 __device__ __forceinline__ bool process_slab(const GraphView& g, bool valid, uint32_t grp, uint32_t olo, uint32_t ohi,
-                                             uint32_t othr, const uint32_t* rk, const SampleConst& sc, int lane,
-                                             uint32_t* stage, unsigned long long& draws, Known&& known,
-                                             Visit&& visit) {
+                                             const uint32_t* rk, const SampleConst& sc, int lane, uint32_t* stage,
+                                             unsigned long long& draws, Known&& known, Visit&& visit) {
   uint32_t cand = 0, u0 = 0, u1 = 0, u2 = 0, u3 = 0;
-  if (WC && valid) {
-    // weighted cascade: every in-edge of the owner has threshold othr, so the
-    // coins need no record; only live edges load their tail
-    const uint32_t e = grp * 4u;
-    const uint32_t a = olo > e ? olo - e : 0u;
-    const uint32_t b = ohi - e;
-    const uint32_t need = (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
-    ++draws;
-    const uint4 r = philox_x(grp, sc, rk);
-    if ((need & 1u) && edge_live(r.x, othr)) cand |= 1u;
-    if ((need & 2u) && edge_live(r.y, othr)) cand |= 2u;
-    if ((need & 4u) && edge_live(r.z, othr)) cand |= 4u;
-    if ((need & 8u) && edge_live(r.w, othr)) cand |= 8u;
-    if (cand) {
-      const uint2* p = g.edge + (size_t)e;
-      if (cand & 1u) u0 = __ldg(&p[0].x);
-      if (cand & 2u) u1 = __ldg(&p[1].x);
-      if (cand & 4u) u2 = __ldg(&p[2].x);
-      if (cand & 8u) u3 = __ldg(&p[3].x);
-    }
-  } else if (valid) {
+  if (valid) {
     const uint32_t e = grp * 4u;
     // edges e..e+3 that belong to the in-list
     const uint32_t a = olo > e ? olo - e : 0u;
@@ -221,110 +216,14 @@ __device__ __forceinline__ bool deliver(uint32_t cand, uint32_t u0, uint32_t u1,
 // take_heavy(...) == HEAVY_ABORT for some lane (the caller hands the sample on).
 constexpr int HEAVY_SKIP = 1, HEAVY_ABORT = 2;
 
-// Weighted-cascade threshold of a node with d in-edges: floor(2^32 / d), and
-// 0xFFFFFFFF (probability 1) for d = 1.
-__device__ __forceinline__ uint32_t wc_threshold(uint32_t d) {
-  return d <= 1u ? 0xFFFFFFFFu : (uint32_t)(0x100000000ull / d);
-}
-
-// Edges of the group `grp` that lie in the in-list [lo, hi), as a 4-bit mask.
-__device__ __forceinline__ uint32_t group_mask(uint32_t grp, uint32_t lo, uint32_t hi) {
-  const uint32_t e = grp * 4u;
-  const uint32_t a = lo > e ? lo - e : 0u;
-  const uint32_t b = hi - e;
-  return (b >= 4u ? 0xFu : ((1u << b) - 1u)) & ((0xFu << a) & 0xFu);
-}
-
-// Live coins of a Philox draw against one threshold below 0xFFFFFFFF.
-__device__ __forceinline__ uint32_t coins_below(const uint4& r, uint32_t thr) {
-  return (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
-         ((uint32_t)(r.w < thr) << 3);
-}
-
-template <class Visit>
-__device__ __forceinline__ bool deliver_group(const GraphView& g, uint32_t grp, uint32_t cand, int lane,
-                                              uint32_t* stage, Visit&& visit) {
-  uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0;
-  if (cand) {
-    const uint2* p = g.edge + (size_t)grp * 4u;
-    if (cand & 1u) u0 = __ldg(&p[0].x);
-    if (cand & 2u) u1 = __ldg(&p[1].x);
-    if (cand & 4u) u2 = __ldg(&p[2].x);
-    if (cand & 8u) u3 = __ldg(&p[3].x);
-  }
-  return deliver(cand, u0, u1, u2, u3, lane, stage, visit);
-}
-
-// Weighted cascade: one slab of an in-list [lo, hi) of a node with threshold
-// thr (d >= 2, so thr < 0xFFFFFFFF): the WC_SLAB groups from group b on (up
-// to the list's last group g1 - 1), four per lane.  A group's coins are its
-// Philox draw against thr; only live edges load a record, and the rare slab
-// with a live coin goes through deliver().  A full slab runs its four draws
-// per lane unconditionally, as independent chains.  Returns visit's "stop".
-constexpr uint32_t WC_SLAB = 128;
-
-template <class Visit>
-__device__ __forceinline__ bool wc_slab(const GraphView& g, uint32_t lo, uint32_t hi, uint32_t thr, uint32_t b,
-                                        uint32_t g1, const uint32_t* rk, const SampleConst& sc, int lane,
-                                        uint32_t* stage, unsigned long long& draws, Visit&& visit) {
-  uint32_t c[4];
-  if (b + WC_SLAB <= g1) {
-    uint4 r[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) r[u] = philox_x(b + (uint32_t)(32 * u + lane), sc, rk);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) c[u] = coins_below(r[u], thr);
-    draws += 4;
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t gg = b + (uint32_t)(32 * u + lane);
-      c[u] = 0u;
-      if (gg < g1) {
-        c[u] = coins_below(philox_x(gg, sc, rk), thr);
-        ++draws;
-      }
-    }
-  }
-  if (!__any_sync(FULL_MASK, (c[0] | c[1] | c[2] | c[3]) != 0u)) return false;
-#pragma unroll 1
-  for (int u = 0; u < 4; ++u) {
-    const uint32_t gg = b + (uint32_t)(32 * u + lane);
-    const uint32_t cu = c[u] ? (c[u] & group_mask(gg, lo, hi)) : 0u;
-    if (deliver_group(g, gg, cu, lane, stage, visit)) return true;
-  }
-  return false;
-}
-
-// A whole in-list walked by one warp, slab after slab.
-template <class Visit>
-__device__ __forceinline__ bool wc_walk(const GraphView& g, uint32_t lo, uint32_t hi, uint32_t thr,
-                                        const uint32_t* rk, const SampleConst& sc, int lane, uint32_t* stage,
-                                        unsigned long long& draws, Visit&& visit) {
-  const uint32_t g1 = (hi + 3) >> 2;
-  for (uint32_t b = lo >> 2; b < g1; b += WC_SLAB)
-    if (wc_slab(g, lo, hi, thr, b, g1, rk, sc, lane, stage, draws, visit)) return true;
-  return false;
-}
-
-// In the weighted-cascade CTA tier, in-lists of more than this many groups are
-// split into slabs that any warp of the CTA takes.
-constexpr int WC_SPLIT_GROUPS = 2 * (int)WC_SLAB - 1;
-
-// In-lists of at least this many 4-edge groups are walked by the whole warp
-// alone (weighted cascade): no owner search per group.
-constexpr int WC_SOLO_GROUPS = 64;
-
-template <bool WC, class Known, class Visit, class Heavy>
+template <class Known, class Visit, class Heavy>
 __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& sc,
                                          int lane, uint32_t* stage, unsigned long long& ev, unsigned long long& draws,
                                          int heavy_groups, Known&& known, Visit&& visit, Heavy&& take_heavy) {
   uint32_t lo = 0, hi = 0;  // edge positions fit 32 bits (m < 2^31)
-  uint32_t thr = 0;
   if (v >= 0) {
     lo = (uint32_t)__ldg(g.off + v);
     hi = (uint32_t)__ldg(g.off + v + 1);
-    if (WC) thr = wc_threshold(hi - lo);
   }
   int ng = (hi > lo) ? (int)(((hi + 3) >> 2) - (lo >> 2)) : 0;
   int heavy = 0;
@@ -332,18 +231,6 @@ __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const ui
   if (__any_sync(FULL_MASK, heavy == HEAVY_ABORT)) return 2;
   if (heavy == HEAVY_SKIP) ng = 0;  // counted and expanded by the taker
   else ev += hi - lo;
-  if (WC) {
-    // long lists first, each by the whole warp
-    unsigned solo = __ballot_sync(FULL_MASK, ng >= WC_SOLO_GROUPS);
-    if (ng >= WC_SOLO_GROUPS) ng = 0;
-    while (solo) {
-      const int sl = __ffs(solo) - 1;
-      solo &= solo - 1u;
-      const uint32_t slo = __shfl_sync(FULL_MASK, lo, sl), shi = __shfl_sync(FULL_MASK, hi, sl);
-      const uint32_t sthr = __shfl_sync(FULL_MASK, thr, sl);
-      if (wc_walk(g, slo, shi, sthr, rk, sc, lane, stage, draws, visit)) return 1;
-    }
-  }
   const int incl = warp_inclusive_scan(ng, lane);
   const int excl = incl - ng;
   const int total = __shfl_sync(FULL_MASK, incl, 31);
@@ -358,12 +245,102 @@ __device__ __forceinline__ int expand_ic(const GraphView& g, int32_t v, const ui
     owner = owner > 31 ? 31 : owner;
     const uint32_t olo = __shfl_sync(FULL_MASK, lo, owner);
     const uint32_t ohi = __shfl_sync(FULL_MASK, hi, owner);
-    const uint32_t othr = WC ? __shfl_sync(FULL_MASK, thr, owner) : 0u;
     const int oex = __shfl_sync(FULL_MASK, excl, owner);
     const uint32_t grp = (olo >> 2) + (uint32_t)(q - oex);
-    if (process_slab<WC>(g, q < total, grp, olo, ohi, othr, rk, sc, lane, stage, draws, known, visit)) return 1;
+    if (process_slab(g, q < total, grp, olo, ohi, rk, sc, lane, stage, draws, known, visit)) return 1;
   }
   return 0;
+}
+
+// Weighted-cascade threshold of a node with d in-edges: floor(2^32 / d), and
+// 0xFFFFFFFF (probability 1) for d = 1.
+__device__ __forceinline__ uint32_t wc_threshold(uint32_t d) {
+  return d <= 1u ? 0xFFFFFFFFu : (uint32_t)(0x100000000ull / d);
+}
+
+// Gap form of weighted cascade.  All d >= 2 in-edges of a node are live with
+// p = t / 2^32 (t = wc_threshold(d)), so the run G of dead edges before the
+// next live one has P(G >= g) = q^g, q = 1 - p.  In Q64 integers (x in [0,1)
+// as floor(x 2^64), products truncated): Q = (2^32 - t) << 32, P_0 = Q,
+// P_(i+1) = hi64(P_i * P_i); G(U) sets bits J-1 .. 0 in turn (J the bit
+// length of d, so 2^J - 1 >= d), bit i when U < hi64(A * P_i), A the product
+// of the powers already taken (P_i alone for the first), which then becomes
+// A.  G(U) is the largest g with U < q^g up to the truncation.  Each power is
+// rebuilt from Q by squaring where it is needed (no table in registers).
+__device__ __forceinline__ uint32_t wc_gap(uint64_t Q, int J, uint64_t U) {
+  uint64_t A = 0;
+  bool first = true;
+  uint32_t gap = 0;
+  for (int i = J - 1; i >= 0; --i) {
+    uint64_t p = Q;
+    for (int s = 0; s < i; ++s) p = __umul64hi(p, p);
+    const uint64_t cand = first ? p : __umul64hi(A, p);
+    if (U < cand) {
+      A = cand;
+      first = false;
+      gap |= 1u << i;
+    }
+  }
+  return gap;
+}
+
+// Weighted-cascade IC expansion of up to 32 frontier nodes, one per lane
+// (v = -1 for none).  Each lane walks its node's in-list [lo, lo + d): d = 1
+// is one live edge (probability 1); otherwise gap c takes the 64-bit uniform
+// of words 2(c&1), 2(c&1)+1 of the SKIP draw with counter words (v, c >> 1),
+// the next live edge is lo + pos + G, and the walk ends when G reaches past
+// the list.  Every round hands one live tail per lane to visit(u, lt_mask)
+// (NO_NODE for idle lanes).  Returns visit's "stop".
+template <class Visit>
+__device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& skc,
+                                          int lane, unsigned long long& ev, unsigned long long& draws,
+                                          Visit&& visit) {
+  uint32_t lo = 0, d = 0;
+  if (v >= 0) {
+    lo = (uint32_t)__ldg(g.off + v);
+    d = (uint32_t)__ldg(g.off + v + 1) - lo;
+  }
+  ev += d;
+  const uint64_t Q = d >= 2u ? (0x100000000ull - wc_threshold(d)) << 32 : 0ull;
+  const int J = 32 - __clz((int)d);
+  uint32_t pos = 0, c = 0;
+  uint64_t spare = 0;
+  bool active = d > 0u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  while (__any_sync(FULL_MASK, active)) {
+    uint32_t u = NO_NODE;
+    if (active) {
+      uint32_t e = 0;
+      bool live = true;
+      if (d == 1u) {
+        e = lo;
+        active = false;
+      } else {
+        uint64_t U;
+        if (!(c & 1u)) {
+          const uint4 r = philox_xy((uint32_t)v, c >> 1, skc, rk);
+          ++draws;
+          U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+          spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
+        } else {
+          U = spare;
+        }
+        const uint32_t G = wc_gap(Q, J, U);
+        if (G >= d - pos) {
+          live = false;
+          active = false;
+        } else {
+          e = lo + pos + G;
+          pos += G + 1u;
+          ++c;
+          if (pos >= d) active = false;
+        }
+      }
+      if (live) u = __ldg(&g.edge[e].x);
+    }
+    if (visit(u, lt_mask)) return true;
+  }
+  return false;
 }
 
 __device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev, unsigned long long nv,
@@ -419,7 +396,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
   constexpr int HBITS = Tier<TIER>::HBITS, QCAP = Tier<TIER>::QCAP;
   __shared__ __align__(16) uint32_t s_hash[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_HASH : 4];
   __shared__ int32_t s_q[TIER == 0 ? WT_WARPS : 1][TIER == 0 ? WT_QCAP : 4];
-  __shared__ uint32_t s_stage[WT_WARPS][STAGE];
+  __shared__ uint32_t s_stage[WT_WARPS][WC ? 1 : STAGE];  // the gap walk needs no staging
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const size_t gwarp = (size_t)blockIdx.x * WT_WARPS + wid;
   uint32_t* H = TIER == 0 ? s_hash[wid] : J.mid_hash + gwarp * MID_HASH;
@@ -441,7 +418,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= count) break;
     const int64_t j = TIER == 0 ? sample_at(J, idx) : J.mid_list[idx];
-    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
+    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(WC ? PURPOSE_SKIP : PURPOSE_IC, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) {
       const uint32_t h0 = hash_slot<HBITS>((uint32_t)root);
@@ -477,6 +454,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
       return overflow || hit;
     };
     // a node with a very long in-list needs many warps: hand the sample to the CTA tier
+    // (weighted cascade: no in-list is long, its gap walk costs the same at any degree)
     auto to_cta = [](int32_t, uint32_t, uint32_t, int) { return HEAVY_ABORT; };
     bool handoff = false;
     while (head < tail && !overflow && !hit) {
@@ -484,8 +462,10 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      if (expand_ic<WC>(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
-          2) {
+      if constexpr (WC) {
+        expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
+      } else if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
+                 2) {
         handoff = true;
         break;
       }
@@ -527,16 +507,14 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
 
 // Weighted-cascade IC, one warp per sample of up to GQ_CAP nodes, with the
 // visited set as a per-warp n-bit bitmap in global memory and the BFS queue in
-// global memory.  Under weighted cascade a visited node costs one atomicOr
-// against the thousands of coins of a typical in-list, so one tier serves
-// every set size without a hand-over: long in-lists are walked by the whole
-// warp (wc_walk), and only sets that outgrow the queue go to the CTA tier.
+// global memory: one tier for every set size up to the queue, where the
+// hash tiers stop at 512 and 16384 nodes.  Sets that outgrow the queue go to
+// the CTA tier.
 constexpr int GQ_CAP = 1 << 16;
 constexpr int GQ_SLOTS = GQ_CAP + 32;  // room for one round past the cap
 
 template <int MODE>
 __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob J) {
-  __shared__ uint32_t s_stage[WT_WARPS][STAGE];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const size_t gwarp = (size_t)blockIdx.x * WT_WARPS + wid;
   uint32_t* bits = J.wg_bitmap + gwarp * (size_t)J.bitmap_words;
@@ -548,7 +526,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= (unsigned long long)J.count) break;
     const int64_t j = sample_at(J, idx);
-    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
+    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_SKIP, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) {
       atomicOr(bits + (root >> 5), 1u << (root & 31));
@@ -558,7 +536,6 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
     bool overflow = false;
     bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
     __syncwarp();
-    auto known = [](uint32_t) { return false; };
     auto visit = [&](uint32_t u, unsigned lt_mask) -> bool {
       bool is_new = false;
       if (u != NO_NODE) {
@@ -576,24 +553,16 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
       if (tail > GQ_CAP) overflow = true;
       return overflow || hit;
     };
-    // an in-list of more than warp_heavy_groups groups (a hub) hands the sample to the CTA tier,
-    // whose warps split long lists between them
-    auto to_cta = [](int32_t, uint32_t, uint32_t, int) { return HEAVY_ABORT; };
-    bool handoff = false;
     while (head < tail && !overflow && !hit) {
       const int cnt = min(32, tail - head);
       __syncwarp();
       const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
       __syncwarp();
-      if (expand_ic<true>(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
-          2) {
-        handoff = true;
-        break;
-      }
+      expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
       head += cnt;
     }
     __syncwarp();
-    if (overflow || handoff) {
+    if (overflow) {
       if (lane == 0) {
         const unsigned long long b = atomicAdd(&J.ctr->big_count, 1ull);
         J.big_list[b] = j;
@@ -710,14 +679,13 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
   __shared__ long long s_item;
   __shared__ int s_tail, s_next, s_hit, s_ok;
   __shared__ unsigned long long s_pos;
-  __shared__ uint32_t s_stage[WARPS][STAGE];
+  __shared__ uint32_t s_stage[WARPS][WC ? 1 : STAGE];
   // heavy in-lists of the current level, expanded by all warps together
-  __shared__ uint32_t s_hlo[CTA_HEAVY_CAP], s_hhi[CTA_HEAVY_CAP], s_hthr[WC ? CTA_HEAVY_CAP : 1];
-  __shared__ int s_hpref[CTA_HEAVY_CAP];  // weighted cascade: slab count of each split list (0: not posted)
+  __shared__ uint32_t s_hlo[WC ? 1 : CTA_HEAVY_CAP], s_hhi[WC ? 1 : CTA_HEAVY_CAP];
+  __shared__ int s_hpref[WC ? 1 : CTA_HEAVY_CAP];
   __shared__ int s_nheavy, s_htotal, s_hnext;
-  // weighted cascade: queue head, warps holding work, split lists and their slab cursors
-  __shared__ int s_head, s_active, s_nsplit;
-  __shared__ int s_hnext_slab[WC ? CTA_HEAVY_CAP : 1];
+  // weighted cascade: queue head and the warps holding work
+  __shared__ int s_head, s_active;
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
   const int64_t n = J.g.n;
   const int64_t qcap = KIND == 1 ? (int64_t)J.small_qcap : n;
@@ -748,7 +716,7 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
     }
     __syncthreads();
     if (J.model == 0) {
-      const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_IC, J.stream, j));
+      const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(WC ? PURPOSE_SKIP : PURPOSE_IC, J.stream, j));
       // a stale 0 only costs a draw; bits are never cleared during a sample.  With the
       // bitmap in global memory the check would cost an L2 round trip per group, more
       // than the draw it can save, so only the shared-memory bitmap is consulted.
@@ -779,78 +747,25 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
       };
       if constexpr (WC) {
         // Weighted cascade without level barriers: any visiting order reaches
-        // the same set (the coins are keyed per edge), so the warps pull work
-        // as it appears -- up to 32 queued nodes at a time, or one slab of a
-        // long in-list that a warp posted to the split table -- and the sample
-        // ends when nothing is queued or split and no warp holds work.  A
-        // queue slot reads -1 until its node is written, so a claimed slot
-        // whose writer has reserved but not yet stored it is waited for.
-        auto take_split = [&](int32_t, uint32_t lo, uint32_t hi, int) -> int {
-          const int slot = atomicAdd(&s_nsplit, 1);
-          if (slot >= CTA_HEAVY_CAP) return 0;  // table full: this warp walks the list itself
-          s_hlo[slot] = lo;
-          s_hhi[slot] = hi;
-          s_hthr[slot] = wc_threshold(hi - lo);
-          s_hnext_slab[slot] = 0;
-          __threadfence_block();
-          *(volatile int*)&s_hpref[slot] = (int)((((hi + 3) >> 2) - (lo >> 2) + WC_SLAB - 1) / WC_SLAB);
-          ev += hi - lo;
-          return HEAVY_SKIP;
-        };
+        // the same set (the gaps are keyed per node), so the warps pull up to
+        // 32 queued nodes at a time as they appear, and the sample ends when
+        // nothing is queued and no warp holds work.  A queue slot reads -1
+        // until its node is written, so a claimed slot whose writer has
+        // reserved but not yet stored it is waited for.
         auto stopped = [&]() -> bool {
           return (MODE == MODE_HIT && *(volatile int*)&s_hit) || (KIND == 1 && *(volatile int*)&s_tail > qcap);
         };
         if (tid == 0) {
           s_head = 0;
           s_active = 0;
-          s_nsplit = 0;
         }
-        for (int i = tid; i < CTA_HEAVY_CAP; i += nthr) s_hpref[i] = 0;  // slab counts: 0 = not posted yet
         __syncthreads();
         const int qlim = (int)(qcap < 0x7FFFFFFF ? qcap : 0x7FFFFFFF);  // queue slots that can be written
-        int split_from = 0;  // lane 0: split slots below this are exhausted
         long long idle = 0;
         // Every claim and every decision is taken by lane 0 and broadcast, so
         // the warp stays converged for the shuffles and ballots below.
         for (;;) {
           if (__any_sync(FULL_MASK, stopped())) break;
-          // (a) a slab of a posted long list
-          int slot = -1, sl = 0;
-          if (lane == 0) {
-            const int nsplit = min(*(volatile int*)&s_nsplit, CTA_HEAVY_CAP);
-            for (int i = split_from; i < nsplit; ++i) {
-              const int ns = *(volatile int*)&s_hpref[i];
-              if (ns == 0) continue;  // still being posted
-              if (*(volatile int*)&s_hnext_slab[i] >= ns) {
-                if (i == split_from) ++split_from;
-                continue;
-              }
-              atomicAdd(&s_active, 1);
-              const int x = atomicAdd(&s_hnext_slab[i], 1);
-              if (x < ns) {
-                slot = i;
-                sl = x;
-                break;
-              }
-              atomicSub(&s_active, 1);
-            }
-          }
-          slot = __shfl_sync(FULL_MASK, slot, 0);
-          sl = __shfl_sync(FULL_MASK, sl, 0);
-          if (slot >= 0) {
-            __threadfence_block();
-            const uint32_t hlo = s_hlo[slot], hhi = s_hhi[slot];
-            wc_slab(J.g, hlo, hhi, s_hthr[slot], (hlo >> 2) + (uint32_t)sl * WC_SLAB, (hhi + 3) >> 2, J.rk, sc, lane,
-                    stage, dr, visit);
-            __syncwarp();
-            if (lane == 0) {
-              __threadfence_block();  // new queue entries and splits before letting go
-              atomicSub(&s_active, 1);
-            }
-            idle = 0;
-            continue;
-          }
-          // (b) up to 32 queued nodes
           int h = 0, cnt = 0;
           if (lane == 0) {
             atomicAdd(&s_active, 1);
@@ -876,25 +791,20 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
                 }
               }
             }
-            expand_ic<true>(J.g, v, J.rk, sc, lane, stage, ev, dr, WC_SPLIT_GROUPS, known, visit, take_split);
+            expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
             __syncwarp();
             if (lane == 0) {
-              __threadfence_block();  // new queue entries and splits before letting go
+              __threadfence_block();  // new queue entries before letting go
               atomicSub(&s_active, 1);
             }
             idle = 0;
             continue;
           }
-          // (c) nothing to claim: the sample is done once no warp holds work
+          // nothing to claim: the sample is done once no warp holds work
           int done = 0;
           if (lane == 0 && *(volatile int*)&s_active == 0) {
             __threadfence_block();
             done = *(volatile int*)&s_head >= min(*(volatile int*)&s_tail, qlim);
-            const int ns2 = min(*(volatile int*)&s_nsplit, CTA_HEAVY_CAP);
-            for (int i = 0; i < ns2 && done; ++i) {
-              const int ns = *(volatile int*)&s_hpref[i];
-              if (ns == 0 || *(volatile int*)&s_hnext_slab[i] < ns) done = 0;
-            }
           }
           if (__shfl_sync(FULL_MASK, done, 0)) break;
           if (++idle > (1ll << 24)) {  // far longer than any sample: give up and report
@@ -929,7 +839,7 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
           if (b >= lvl_end) break;
           const int cnt = min(32, lvl_end - b);
           const int32_t v = (lane < cnt) ? Q[b + lane] : -1;
-          if (expand_ic<false>(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy))
+          if (expand_ic(J.g, v, J.rk, sc, lane, stage, ev, dr, CTA_HEAVY_GROUPS, known, visit, take_heavy))
             break;
         }
         __syncthreads();
@@ -963,7 +873,7 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
               if (it + step < nh && s_hpref[it + step] <= q) it += step;
             const uint32_t olo = s_hlo[it], ohi = s_hhi[it];
             const uint32_t grp = (olo >> 2) + (uint32_t)(q - s_hpref[it]);
-            if (process_slab<false>(J.g, q < htotal, grp, olo, ohi, 0u, J.rk, sc, lane, stage, dr, known, visit))
+            if (process_slab(J.g, q < htotal, grp, olo, ohi, J.rk, sc, lane, stage, dr, known, visit))
               break;
           }
         }

@@ -12,7 +12,9 @@ arithmetic to the mathematics, not to itself:
   thresholds, over in-degrees from 2 to 2^31 - 1;
 * whole in-lists against the law of d independent coins: on a star whose
   centre is always the source, the number of live in-edges follows
-  Binomial(d, p) exactly and every edge is equally likely to be live.
+  Binomial(d, p) exactly and every edge is equally likely to be live;
+* whole RR sets on an R-MAT graph against the oracle's per-edge-coin path fed
+  the same thresholds.
 """
 import math
 
@@ -94,7 +96,7 @@ def test_star_live_count_is_binomial(orc, d):
     p = ((1 << 32) // d) / float(1 << 32)
     pmf = binom.pmf(np.arange(d + 1), d, p)
     # pool the tail so every cell expects at least 20 sets
-    cells, exp, obs = [], [], []
+    exp, obs = [], []
     acc_e, acc_o = 0.0, 0
     hist = np.bincount(K, minlength=d + 1)
     for k in range(d + 1):
@@ -132,3 +134,31 @@ def test_star_mean_matches_coins_at_a_hub(orc):
     # P(K = 0) = q^d
     p0 = (1 - p) ** d
     assert abs((K == 0).mean() - p0) < 5 * math.sqrt(p0 * (1 - p0) / N)
+
+
+def test_gap_form_matches_coins_on_rmat(orc):
+    """Whole RR sets: the weighted-cascade gap form against independent per-edge
+    coins of the same probabilities (the explicit-threshold path with
+    t = floor(2^32 / d_in), which draws one coin per in-edge), on an R-MAT
+    graph: same distribution of set sizes (two-sample KS), same mean size and
+    the same coverage of the most covered nodes."""
+    from scipy.stats import ks_2samp
+
+    el = inputs.rmat(14, 1 << 17, seed=1)
+    d_in = np.bincount(el.dst, minlength=el.n)
+    thr = np.where(d_in[el.dst] == 1, 0xFFFFFFFF, (1 << 32) // np.maximum(d_in[el.dst], 1)).astype(np.uint32)
+    g_gap = orc.Graph.from_edges(el, orc.W_WC)
+    g_coin = orc.Graph(el.n, el.src, el.dst, orc.W_EXPLICIT, thr=thr)
+    assert np.array_equal(g_gap.csr()[2], g_coin.csr()[2])  # the same thresholds, edge by edge
+    N = 200_000
+    res = []
+    for g in (g_gap, g_coin):
+        off, nodes = orc.Pool(g, orc.IC, seed=7).grow(N).arrays()
+        res.append((np.diff(off), np.bincount(nodes, minlength=el.n)))
+    (s_gap, c_gap), (s_coin, c_coin) = res
+    assert ks_2samp(s_gap, s_coin).pvalue > 1e-3
+    se = math.sqrt((s_gap.var() + s_coin.var()) / N)
+    assert abs(s_gap.mean() - s_coin.mean()) < 5 * se
+    top = np.argsort(-c_coin)[:50]
+    z = (c_gap[top] - c_coin[top]) / np.sqrt(c_gap[top] + c_coin[top])
+    assert np.abs(z).max() < 5
