@@ -148,7 +148,8 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
  * ssa_autotune times a pilot batch of pilot_samples sets (0 = 8192) under the
  * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never}, after one
  * untimed pass that sizes the pilot pool, and keeps the fastest in the graph
- * handle; an IC solve on an untuned graph first tunes it on 4096 sets.  Under
+ * handle; an IC solve on an untuned graph first tunes it on 4096 sets (65536
+ * under SSA_W_WC, whose large sets are rare).  Under
  * SSA_W_WC the in-lists are walked by gaps and none is heavy: the candidates
  * are mid_cap in {0, 16384} and the global-bitmap warp tier of
  * ssa_set_warp_tier where it exists.

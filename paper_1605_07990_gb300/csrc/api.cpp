@@ -1212,7 +1212,9 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
       std::lock_guard<std::mutex> lock(g->tune_mu);
       tuned = g->tuned_mid_cap >= 0;
     }
-    if (!tuned) TRY(autotune_ic(g, 4096, X, nullptr, nullptr));
+    // weighted-cascade sets are mostly one node with a long tail: a pilot of
+    // 4096 holds too few large sets to rank the tiers
+    if (!tuned) TRY(autotune_ic(g, g->weighting == SSA_W_WC ? 65536 : 4096, X, nullptr, nullptr));
     X.launches = 0;
   }
   Sampler& S = sv->S[p->model];

@@ -265,16 +265,22 @@ __device__ __forceinline__ uint32_t wc_threshold(uint32_t d) {
 // P_(i+1) = hi64(P_i * P_i); G(U) sets bits J-1 .. 0 in turn (J the bit
 // length of d, so 2^J - 1 >= d), bit i when U < hi64(A * P_i), A the product
 // of the powers already taken (P_i alone for the first), which then becomes
-// A.  G(U) is the largest g with U < q^g up to the truncation.  Each power is
-// rebuilt from Q by squaring where it is needed (no table in registers).
-__device__ __forceinline__ uint32_t wc_gap(uint64_t Q, int J, uint64_t U) {
+// A.  G(U) is the largest g with U < q^g up to the truncation.  The powers of
+// a node are built once, into the lane's own table P (J <= 31 entries).
+__device__ __forceinline__ void wc_powers(uint64_t Q, int J, uint64_t* P) {
+  uint64_t p = Q;
+  for (int i = 0; i < J; ++i) {
+    P[i] = p;
+    p = __umul64hi(p, p);
+  }
+}
+
+__device__ __forceinline__ uint32_t wc_gap(const uint64_t* P, int J, uint64_t U) {
   uint64_t A = 0;
   bool first = true;
   uint32_t gap = 0;
   for (int i = J - 1; i >= 0; --i) {
-    uint64_t p = Q;
-    for (int s = 0; s < i; ++s) p = __umul64hi(p, p);
-    const uint64_t cand = first ? p : __umul64hi(A, p);
+    const uint64_t cand = first ? P[i] : __umul64hi(A, P[i]);
     if (U < cand) {
       A = cand;
       first = false;
@@ -301,8 +307,9 @@ __device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const u
     d = (uint32_t)__ldg(g.off + v + 1) - lo;
   }
   ev += d;
-  const uint64_t Q = d >= 2u ? (0x100000000ull - wc_threshold(d)) << 32 : 0ull;
   const int J = 32 - __clz((int)d);
+  uint64_t P[31];  // q^(2^i), i < J (per lane; J <= 31 as d < 2^31)
+  if (d >= 2u) wc_powers((0x100000000ull - wc_threshold(d)) << 32, J, P);
   uint32_t pos = 0, c = 0;
   uint64_t spare = 0;
   bool active = d > 0u;
@@ -325,7 +332,7 @@ __device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const u
         } else {
           U = spare;
         }
-        const uint32_t G = wc_gap(Q, J, U);
+        const uint32_t G = wc_gap(P, J, U);
         if (G >= d - pos) {
           live = false;
           active = false;
