@@ -52,11 +52,14 @@ EXTRA = "dssa_ic_trivalency_rmat20_m16M_k100"
 METRIC, UNIT = "RR sets/s", "RR sets/s"
 WEIGHTS = ["weighted-cascade", "trivalency"]
 
-# ALU roofline of the IC samplers.  Each coin comes from one Philox4x32-10 draw
-# per 4-edge group: 10 rounds of two 32x32->64 multiplies and two three-input
-# XORs, 40 thread instructions at least.  At one warp instruction per SM
-# sub-partition per clock (4 per SM) the GPU issues at most
+# ALU roofline of the IC samplers with edge records (trivalency, explicit
+# weights).  Each coin comes from one Philox4x32-10 draw per 4-edge group: 10
+# rounds of two 32x32->64 multiplies and two three-input XORs, 40 thread
+# instructions at least.  At one warp instruction per SM sub-partition per
+# clock (4 per SM) the GPU issues at most
 #   SMs x 4 x clock x 32 lanes / 40 draws per second.
+# The weighted-cascade sampler walks in-lists by geometric gaps (one draw per
+# two gaps, no per-edge coins) and is reported against HBM instead.
 PHILOX_MIN_INSTR = 40
 
 # DRAM bytes per unit of work from ncu captures of the sampler kernels
@@ -169,17 +172,15 @@ def sampler_model(weighting, model):
 
 
 def roofline(kind, dom, ks, results, sm_count, clock_mhz, name, hbm_peak, hbm_kind):
-    """Roofline of the dominant kernel class.
+    """Roofline of the dominant kernel class (a sampler tier).
 
-    The IC samplers draw one Philox4x32-10 per 4-edge group; with weighted-cascade
-    weights the coins need no edge record (thresholds follow from in-degrees)
-    and the kernel is bound by integer issue, so it is reported in draws/s
-    against PHILOX_MIN_INSTR.  Algorithmic bytes per unit (for the HBM side
-    figure): weighted cascade, 16 per visited node (two CSR offsets) + 8 per
-    live edge taken (one record; at least one per visited node but the root)
-    + 8 per stored pool entry + 12 per stored set + 1 per hit-tested set;
-    edge records (trivalency, explicit), 8 per examined in-edge instead of the
-    per-live-edge record."""
+    Weighted-cascade IC (gap walk): bound "hbm".  Algorithmic bytes per unit:
+    16 per visited node (two CSR offsets), 8 per live edge taken (its record;
+    one per visited node but the root), 8 per stored pool entry (node,
+    sample), 12 per stored set (start, length), 1 per hit-tested set.  No
+    per-edge bytes: the gaps need only the in-degree.
+    Edge records (trivalency, explicit): bound "alu" in Philox draws/s against
+    PHILOX_MIN_INSTR, with 8 per examined in-edge in the HBM side figure."""
     if dom not in ("sample_cta", "sample_warp") or kind == "lt" or ks[dom]["ms"] <= 0:
         return None
     cta = dom == "sample_cta"
@@ -190,22 +191,28 @@ def roofline(kind, dom, ks, results, sm_count, clock_mhz, name, hbm_peak, hbm_ki
     st_e = sum((r.cta_stored_entries if cta else r.pool_entries - r.cta_stored_entries) for r in results)
     st_s = sum((r.cta_stored_sets if cta else r.trace[-1]["n_sets"] - r.cta_stored_sets) for r in results)
     sec = ks[dom]["ms"] / 1000.0
-    peak = sm_count * 4 * clock_mhz * 1e6 * 32 / PHILOX_MIN_INSTR
-    ach = draws / sec
-    if kind == "ic_wc":
-        abytes = 16 * nv + 8 * max(nv - sets, 0) + 8 * st_e + 12 * st_s + max(sets - st_s, 0)
-    else:
-        abytes = 8 * ev + 16 * nv + 8 * st_e + 12 * st_s + max(sets - st_s, 0)
     launches = max(1, ks[dom]["launches"])
     tr = TRAFFIC.get((name, dom))
     traffic = None
     if tr and tr["src"] == kernel_source_hash():
         traffic = tr["bytes_per_node_visit"] * nv / launches
-    return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Philox draws/s",
+    common = {"kernel": dom, "traffic": traffic, "avg_launch_ms": ks[dom]["ms"] / launches,
+              "node_visits_per_launch": nv / launches, "node_visits_per_s": nv / sec,
+              "philox_draws_per_s": draws / sec}
+    if kind == "ic_wc":
+        abytes = 16 * nv + 8 * max(nv - sets, 0) + 8 * st_e + 12 * st_s + max(sets - st_s, 0)
+        ach = abytes / sec / 1e9
+        return {**common, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": hbm_kind,
+                "algorithmic_bytes_per_launch": abytes / launches,
+                "implied_edge_visits_per_s": ev / sec}
+    peak = sm_count * 4 * clock_mhz * 1e6 * 32 / PHILOX_MIN_INSTR
+    ach = draws / sec
+    abytes = 8 * ev + 16 * nv + 8 * st_e + 12 * st_s + max(sets - st_s, 0)
+    return {**common, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Philox draws/s",
             "frac": ach / peak,
             "peak_source": f"derived: {sm_count} SMs x 4 issue slots x {clock_mhz:.0f} MHz x 32 lanes / "
                            f"{PHILOX_MIN_INSTR} instructions per Philox4x32-10 draw",
-            "traffic": traffic, "avg_launch_ms": ks[dom]["ms"] / launches,
             "draws_per_launch": draws / launches, "edge_visits_per_launch": ev / launches,
             "hbm": {"algorithmic_bytes_per_launch": abytes / launches, "algorithmic_gbs": abytes / sec / 1e9,
                     "peak_gbs": hbm_peak, "frac": abytes / sec / 1e9 / hbm_peak, "peak_source": hbm_kind}}
@@ -467,7 +474,8 @@ def main():
     ap.add_argument("--then-greedy", type=int, default=0,
                     help="with --sample-only: also index the pool and run greedy Max-Coverage for this k")
     ap.add_argument("--tune", default="",
-                    help="with --sample-only: IC sampler hand-overs MID_CAP,HEAVY_GROUPS (ssa_set_tuning)")
+                    help="with --sample-only: IC sampler hand-overs MID_CAP,HEAVY_GROUPS[,GLOBAL_BITMAP_TIER] "
+                         "(ssa_set_tuning, ssa_set_warp_tier)")
     ap.add_argument("--serving", action="store_true", help="the Poisson serving mix instead of the solve bench")
     ap.add_argument("--queries", type=int, default=2000, help="queries of --serving")
     ap.add_argument("--serving-queries", type=int, default=120,
@@ -506,8 +514,10 @@ def main():
         og_thread.start()
     if args.sample_only:
         if args.tune:
-            mid, heavy = (int(x) for x in args.tune.split(","))
-            P.ssa_set_tuning(g, mid, heavy)
+            t = [int(x) for x in args.tune.split(",")]
+            P.ssa_set_tuning(g, t[0], t[1])
+            if len(t) > 2:
+                P.ssa_set_warp_tier(g, t[2])
         t0 = time.perf_counter()
         pool = P.Pool(g, model, seed=1, stream=0).grow(args.sample_only)
         torch.cuda.synchronize()

@@ -453,7 +453,7 @@ struct Sampler {
     X.launches += model == 0 ? 3 : 2;
     CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, X.st));
     CU(cudaStreamSynchronize(X.st));
-    if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error");
+    if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error (wait %u gave up)", h_ctr->error);
     return SSA_OK;
   }
 
@@ -589,7 +589,7 @@ struct Sampler {
     return SSA_OK;
   }
   ssa_status hits_finish(int64_t count) {
-    if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error");
+    if (h_ctr->error) return fail(SSA_E_INTERNAL, "sampler reported an internal error (wait %u gave up)", h_ctr->error);
     tally(count);
     hit_samples += count;
     return SSA_OK;

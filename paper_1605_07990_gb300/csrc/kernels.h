@@ -19,6 +19,10 @@ struct GraphView {
 };
 
 // Device counters of one sampling batch.
+// Bounded waits of the weighted-cascade CTA tier that gave up (Counters::error).
+constexpr unsigned SAMPLER_ERR_SLOT = 1;  // a claimed queue slot was never written
+constexpr unsigned SAMPLER_ERR_IDLE = 2;  // a warp found no work for far longer than any sample
+
 struct Counters {
   unsigned long long work;         // warp tier: next sample index
   unsigned long long mid_count;    // samples handed from the shared-memory warp tier to the global one
@@ -37,7 +41,7 @@ struct Counters {
   unsigned long long ok_end;        // end of the last pool reservation that fit
   unsigned long long fail_count;    // samples whose reservation did not fit (listed in fail_list)
   unsigned int pool_overflow;      // a reservation passed pool_cap
-  unsigned int error;              // internal error flag
+  unsigned int error;              // internal error: 0 none, else SAMPLER_ERR_* of the first wait that gave up
 };
 
 enum : int { MODE_STORE = 0, MODE_HIT = 1 };

@@ -691,8 +691,8 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
   __shared__ uint32_t s_hlo[WC ? 1 : CTA_HEAVY_CAP], s_hhi[WC ? 1 : CTA_HEAVY_CAP];
   __shared__ int s_hpref[WC ? 1 : CTA_HEAVY_CAP];
   __shared__ int s_nheavy, s_htotal, s_hnext;
-  // weighted cascade: queue head and the warps holding work
-  __shared__ int s_head, s_active;
+  // weighted cascade: queue head, and nodes queued or being expanded
+  __shared__ int s_head, s_pending;
   const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
   const int64_t n = J.g.n;
   const int64_t qcap = KIND == 1 ? (int64_t)J.small_qcap : n;
@@ -740,7 +740,10 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
         const unsigned m = __ballot_sync(FULL_MASK, is_new);
         int base = 0;
         if (m) {
-          if (lane == 0) base = atomicAdd(&s_tail, __popc(m));
+          if (lane == 0) {
+            if (WC) atomicAdd(&s_pending, __popc(m));  // before the producer's own chunk is retired
+            base = atomicAdd(&s_tail, __popc(m));
+          }
           base = __shfl_sync(FULL_MASK, base, 0);
           if (is_new) {
             const int pos = base + __popc(m & lt_mask);
@@ -755,16 +758,18 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
       if constexpr (WC) {
         // Weighted cascade without level barriers: any visiting order reaches
         // the same set (the gaps are keyed per node), so the warps pull up to
-        // 32 queued nodes at a time as they appear, and the sample ends when
-        // nothing is queued and no warp holds work.  A queue slot reads -1
-        // until its node is written, so a claimed slot whose writer has
-        // reserved but not yet stored it is waited for.
+        // 32 queued nodes at a time as they appear.  s_pending counts the
+        // nodes queued or being expanded: a warp adds the nodes it queues
+        // before it retires the chunk it expanded, so s_pending reaches 0 only
+        // when nothing is queued and no warp holds work, and the sample ends
+        // there.  A queue slot reads -1 until its node is written, so a claimed
+        // slot whose writer has reserved but not yet stored it is waited for.
         auto stopped = [&]() -> bool {
           return (MODE == MODE_HIT && *(volatile int*)&s_hit) || (KIND == 1 && *(volatile int*)&s_tail > qcap);
         };
         if (tid == 0) {
           s_head = 0;
-          s_active = 0;
+          s_pending = 1;  // the root
         }
         __syncthreads();
         const int qlim = (int)(qcap < 0x7FFFFFFF ? qcap : 0x7FFFFFFF);  // queue slots that can be written
@@ -775,14 +780,12 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
           if (__any_sync(FULL_MASK, stopped())) break;
           int h = 0, cnt = 0;
           if (lane == 0) {
-            atomicAdd(&s_active, 1);
             for (;;) {
               h = *(volatile int*)&s_head;
               const int avail = min(*(volatile int*)&s_tail, qlim) - h;
               cnt = avail < 32 ? avail : 32;
               if (cnt <= 0 || atomicCAS(&s_head, h, h + cnt) == h) break;
             }
-            if (cnt <= 0) atomicSub(&s_active, 1);
           }
           h = __shfl_sync(FULL_MASK, h, 0);
           cnt = __shfl_sync(FULL_MASK, cnt, 0);
@@ -792,7 +795,7 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
               // the slot's writer has reserved it; wait (briefly) for its store
               for (long long w = 0; (v = *(volatile int32_t*)&Q[h + lane]) < 0; ++w) {
                 if (w > (1ll << 22)) {
-                  atomicExch(&J.ctr->error, 1u);
+                  atomicCAS(&J.ctr->error, 0u, SAMPLER_ERR_SLOT);
                   v = -1;
                   break;
                 }
@@ -801,21 +804,17 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
             expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
             __syncwarp();
             if (lane == 0) {
-              __threadfence_block();  // new queue entries before letting go
-              atomicSub(&s_active, 1);
+              __threadfence_block();  // new queue entries before the chunk is retired
+              atomicSub(&s_pending, cnt);
             }
             idle = 0;
             continue;
           }
-          // nothing to claim: the sample is done once no warp holds work
-          int done = 0;
-          if (lane == 0 && *(volatile int*)&s_active == 0) {
-            __threadfence_block();
-            done = *(volatile int*)&s_head >= min(*(volatile int*)&s_tail, qlim);
-          }
-          if (__shfl_sync(FULL_MASK, done, 0)) break;
+          // nothing to claim: the sample is done once nothing is pending
+          const int done = *(volatile int*)&s_pending == 0;
+          if (__any_sync(FULL_MASK, done)) break;
           if (++idle > (1ll << 24)) {  // far longer than any sample: give up and report
-            if (lane == 0) atomicExch(&J.ctr->error, 1u);
+            if (lane == 0) atomicCAS(&J.ctr->error, 0u, SAMPLER_ERR_IDLE);
             break;
           }
           __nanosleep(64);
