@@ -149,10 +149,10 @@ ssa_status ssa_graph_export(const ssa_graph* g, int64_t* off, int32_t* src, uint
  * candidates (mid_cap, heavy_groups) in {0, 16384} x {4096, never}, after one
  * untimed pass that sizes the pilot pool, and keeps the fastest in the graph
  * handle; an IC solve on an untuned graph first tunes it on 4096 sets (65536
- * under SSA_W_WC, whose large sets are rare).  Under
- * SSA_W_WC the in-lists are walked by gaps and none is heavy: the candidates
- * are mid_cap in {0, 16384} and the global-bitmap warp tier of
- * ssa_set_warp_tier where it exists.
+ * under SSA_W_WC, whose large sets are rare).  Under SSA_W_WC the in-lists are
+ * walked by gaps and none is heavy: where the global-bitmap warp tier of
+ * ssa_set_warp_tier exists it is chosen without a pilot (*pilot_ms = 0),
+ * else the candidates are mid_cap in {0, 16384}.
  * ssa_set_tuning fixes both by hand (0 <= mid_cap <= 16384, heavy_groups >= 1;
  * 0x7FFFFFFF = never hand over).  Results never depend on the tuning.  For
  * SSA_LT ssa_autotune has nothing to tune. */
@@ -172,6 +172,12 @@ ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue);
  * keeps the hash warp tiers of ssa_set_tuning.  ssa_autotune times this tier
  * where it exists.  Results never depend on it. */
 ssa_status ssa_set_warp_tier(const ssa_graph* g, int32_t global_bitmap);
+/* Weighted-cascade IC: with on = 1 (the default) a lane tier runs before the
+ * warp tiers, one sample per lane with its queue of up to 32 nodes in
+ * thread-local memory; larger sets are redone by the warp tiers.  0
+ * sends every sample to the warp tiers.  Applies to sampling started after
+ * the call; results never depend on it. */
+ssa_status ssa_set_lane_tier(const ssa_graph* g, int32_t on);
 
 /* Process-wide choice of the greedy kernel's launch shape (results never
  * depend on it): 0 (default) uses one thread-block cluster of 16 (or 8) blocks,

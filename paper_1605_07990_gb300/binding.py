@@ -80,6 +80,7 @@ EXPORTS = {
     "ssa_set_greedy_mode": (C.c_int, [C.c_int32]),
     "ssa_set_queue_tuning": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_set_warp_tier": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ssa_set_lane_tier": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssa_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
     "ssa_solver_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "ssa_solver_solve": (C.c_int, [C.c_void_p, C.POINTER(ssa_params), C.POINTER(ssa_result)]),
@@ -223,6 +224,10 @@ def ssa_set_tuning(g: Graph, mid_cap, heavy_groups=0x7FFFFFFF):
 
 def ssa_set_warp_tier(g: Graph, global_bitmap=0):
     _check(lib().ssa_set_warp_tier(g.h, int(global_bitmap)))
+
+
+def ssa_set_lane_tier(g: Graph, on=1):
+    _check(lib().ssa_set_lane_tier(g.h, int(on)))
 
 
 def ssa_set_queue_tuning(g: Graph, small_queue=0):

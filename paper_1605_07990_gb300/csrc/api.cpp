@@ -111,6 +111,7 @@ struct ssa_graph {
   mutable int tuned_heavy = 0x7FFFFFFF;
   mutable int tuned_small_qcap = 0;  // queue of the small CTAs (0: min(n, 2^20))
   mutable int tuned_warp_global = 0;  // weighted-cascade IC: the global-bitmap warp tier takes every sample
+  mutable int tuned_lane_tier = 1;    // weighted-cascade IC: the lane tier runs first
   GraphView view() const {
     GraphView v;
     v.n = n;
@@ -274,6 +275,9 @@ struct Sampler {
   int lt_cumulative = 0;
   int wc_implicit = 0;
   int warp_global = 0;  // weighted-cascade IC: the global-bitmap warp tier takes every sample
+  int lane_tier = 0;    // weighted-cascade IC: the lane tier runs first
+  int64_t* lane_list = nullptr;
+  int64_t lane_cap = 0;
   uint32_t* wg_bitmap = nullptr;
   int32_t* wg_queue = nullptr;
   int mid_cap = 16384;  // IC: largest set the global warp tier keeps (0 = none)
@@ -308,6 +312,7 @@ struct Sampler {
         heavy_groups = G->tuned_heavy;
       }
       warp_global = (G->tuned_warp_global && cfg.wg_blocks > 0) ? 1 : 0;
+      lane_tier = (G->tuned_lane_tier && cfg.lane_blocks > 0) ? 1 : 0;
     }
     X.num_sms = cfg.num_sms;
     edge_visits = node_visits = samples = hit_samples = 0;
@@ -381,6 +386,7 @@ struct Sampler {
     if (h_ctr) cudaFreeHost(h_ctr);
     h_ctr = nullptr;
     dev_free(big_list, st);
+    dev_free(lane_list, st);
     dev_free(mid_list, st);
     dev_free(mid_hash, st);
     dev_free(mid_queue, st);
@@ -406,6 +412,8 @@ struct Sampler {
     J.lt_cumulative = lt_cumulative;
     J.wc_implicit = wc_implicit;
     J.warp_global = warp_global;
+    J.lane_tier = (model == 0 && wc_implicit && lane_tier) ? 1 : 0;
+    J.lane_list = lane_list;
     J.wg_bitmap = wg_bitmap;
     J.wg_queue = wg_queue;
     J.seed = seed;
@@ -443,6 +451,7 @@ struct Sampler {
   ssa_status run(SampleJob& J, Exec& X, unsigned long long cursor0) {
     std::memset(h_ctr, 0, sizeof(Counters));
     h_ctr->cursor = cursor0;
+    h_ctr->ok_end = ~0ull;  // least start of a reservation that did not fit
     CU(cudaMemcpyAsync(d_ctr, h_ctr, sizeof(Counters), cudaMemcpyHostToDevice, X.st));
     int h = X.begin(SSA_K_SAMPLE_WARP);
     CU(launch_sample_warp(J, cfg, X.st));
@@ -472,6 +481,7 @@ struct Sampler {
     const int64_t j0 = P.count;
     if (j0 + count > (int64_t)0x7FFFFFFF) return fail(SSA_E_POOL_FULL, "more than 2^31 RR sets");
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&lane_list, &lane_cap, count, 0, X.st));
     TRY(dev_grow(&big2_list, &big2_cap, count, 0, X.st));
     TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&fail_list, &fail_cap, count, 0, X.st));
@@ -567,6 +577,7 @@ struct Sampler {
   // and read back into pinned memory, then the checks and statistics.
   ssa_status hits_prepare(int64_t count, Exec& X) {
     TRY(dev_grow(&big_list, &big_cap, count, 0, X.st));
+    TRY(dev_grow(&lane_list, &lane_cap, count, 0, X.st));
     TRY(dev_grow(&big2_list, &big2_cap, count, 0, X.st));
     TRY(dev_grow(&mid_list, &mid_list_cap, count, 0, X.st));
     TRY(dev_grow(&hit, &hit_cap, count, 0, X.st));
@@ -1010,9 +1021,21 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
   // heavy: its candidates are the hash tiers and, where the graph has it, the bitmap tier.
   const int cands_thr[4][3] = {{0, 0x7FFFFFFF, 0}, {mid_tier_max_cap(), 0x7FFFFFFF, 0}, {0, 4096, 0},
                                {mid_tier_max_cap(), 4096, 0}};
+  // Where the global-bitmap tier exists it takes every sample: it beat the hash and CTA tiers
+  // on 2M-set batches of the 2^23- and 2^25-node R-MAT graphs by 1.4-1.6x, while a pilot small
+  // enough to time cheaply is ranked by its few largest sets, not by throughput.
   const int cands_wc[3][3] = {{0, 0x7FFFFFFF, 0}, {mid_tier_max_cap(), 0x7FFFFFFF, 0}, {0, 0x7FFFFFFF, 1}};
   const bool wc = G->weighting == SSA_W_WC;
   const int(*cands)[3] = wc ? cands_wc : cands_thr;
+  if (wc && sampler_config(G->view(), 0, true).wg_blocks > 0) {
+    std::lock_guard<std::mutex> lock(G->tune_mu);
+    G->tuned_mid_cap = cands_wc[2][0];
+    G->tuned_heavy = cands_wc[2][1];
+    G->tuned_warp_global = cands_wc[2][2];
+    if (chosen) *chosen = cands_wc[2][0];
+    if (ms_out) *ms_out = 0.0;
+    return SSA_OK;
+  }
   double best_ms = 1e300;
   int best = cands[1][0], best_heavy = cands[1][1], best_global = 0;
   // One sampler and one pool serve every candidate: the tier settings are
@@ -1024,7 +1047,7 @@ ssa_status autotune_ic(const ssa_graph* G, int64_t pilot, Exec& X, int* chosen, 
   ssa_status st = S.init(G, 0, nullptr, X);
   if (st == SSA_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
     st = fail(SSA_E_CUDA, "autotune: cudaEventCreate failed");
-  const int ncand = wc ? (S.cfg.wg_blocks > 0 ? 3 : 2) : 4;
+  const int ncand = wc ? 2 : 4;
   for (int c = -1; c < ncand && st == SSA_OK; ++c) {
     const auto& cand = cands[c < 0 ? 0 : c];
     S.mid_cap = cand[0];
@@ -1622,6 +1645,13 @@ ssa_status ssa_set_warp_tier(const ssa_graph* g, int32_t global_bitmap) {
   if (!g) return fail(SSA_E_ARG, "null graph");
   std::lock_guard<std::mutex> lock(g->tune_mu);
   g->tuned_warp_global = global_bitmap != 0 ? 1 : 0;
+  return SSA_OK;
+}
+
+ssa_status ssa_set_lane_tier(const ssa_graph* g, int32_t on) {
+  if (!g) return fail(SSA_E_ARG, "null graph");
+  std::lock_guard<std::mutex> lock(g->tune_mu);
+  g->tuned_lane_tier = on != 0 ? 1 : 0;
   return SSA_OK;
 }
 

@@ -38,8 +38,11 @@ struct Counters {
   unsigned long long cta_node_visits;
   unsigned long long cta_draws;    // the CTA tier's share of draws
   unsigned long long draws;        // Philox draws (IC: one per 4-edge group that needed coins)
-  unsigned long long ok_end;        // end of the last pool reservation that fit
+  unsigned long long ok_end;        // start of the first pool reservation that did not fit (the
+                                    // host sets ~0 before a storing launch): the ones that fit end there
   unsigned long long fail_count;    // samples whose reservation did not fit (listed in fail_list)
+  unsigned long long lane_work;    // lane tier: next sample index
+  unsigned long long lane_count;   // samples the lane tier handed to the warp tiers
   unsigned int pool_overflow;      // a reservation passed pool_cap
   unsigned int error;              // internal error: 0 none, else SAMPLER_ERR_* of the first wait that gave up
 };
@@ -53,6 +56,9 @@ struct SampleJob {
   int wc_implicit = 0;           // IC with weighted-cascade weights: thresholds from in-degrees,
                                  // records read for live edges only
   int warp_global = 0;           // weighted-cascade IC: every sample through the global-bitmap warp tier
+  int lane_tier = 0;             // weighted-cascade IC: the lane tier runs first; the warp tiers take
+                                 // only the samples it lists in lane_list (capacity `count`)
+  int64_t* lane_list = nullptr;
   uint32_t* wg_bitmap = nullptr; // that tier: per warp bitmap_words words, zero between samples
   int32_t* wg_queue = nullptr;   // that tier: per warp wg_queue_per_warp() entries
   uint64_t seed = 0;
@@ -103,6 +109,7 @@ struct LaunchCfg {
   int small_blocks = 0;  // small CTAs (256 threads) when the bitmap lives in global memory
   int small_qcap = 0;
   int wg_blocks = 0;     // global-bitmap warp tier (0: not available for this graph)
+  int lane_blocks = 0;   // lane tier (weighted-cascade IC)
   bool cta_smem_bitmap = false;
   int64_t smem_bitmap_bytes = 0;
 };

@@ -350,6 +350,76 @@ __device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const u
   return false;
 }
 
+// Weighted-cascade BFS of one sample by one warp over its private queue
+// Q[0, tail) (head = 0 at the start): every lane holds at most one node and
+// takes one gap step per round; a lane whose node is done takes the next
+// queued node at the start of the next round, so the lanes stay busy while
+// the queue holds work (a node's walk is the gap walk of expand_wc, the same
+// keyed draws).  visit(u, lt_mask) appends new nodes to Q and advances tail
+// (which this function reads through the reference); it returns "stop".
+template <class Visit>
+__device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q, const int& tail,
+                                            const uint32_t* rk, const SampleConst& skc, int lane,
+                                            unsigned long long& ev, unsigned long long& draws, Visit&& visit) {
+  const unsigned lt_mask = (1u << lane) - 1u;
+  int head = 0;
+  int32_t v = -1;
+  uint32_t lo = 0, d = 0, pos = 0, c = 0;
+  int Jb = 0;
+  uint64_t spare = 0;
+  uint64_t P[31];  // q^(2^i), i < Jb, of the lane's node
+  for (;;) {
+    __syncwarp();  // queue entries written by other lanes in the last round
+    const bool need = v < 0;
+    const unsigned nm = __ballot_sync(FULL_MASK, need);
+    const int take = min(__popc(nm), tail - head);
+    if (need) {
+      const int r = __popc(nm & lt_mask);
+      if (r < take) {
+        v = Q[head + r];
+        lo = (uint32_t)__ldg(g.off + v);
+        d = (uint32_t)__ldg(g.off + v + 1) - lo;
+        ev += d;
+        pos = 0;
+        c = 0;
+        Jb = 32 - __clz((int)d);
+        if (d >= 2u) wc_powers((0x100000000ull - wc_threshold(d)) << 32, Jb, P);
+      }
+    }
+    head += take;
+    if (!__any_sync(FULL_MASK, v >= 0)) break;  // queue drained, no lane holds a node
+    uint32_t u = NO_NODE;
+    if (v >= 0) {
+      if (d == 0u) {
+        v = -1;
+      } else if (d == 1u) {
+        u = __ldg(&g.edge[lo].x);
+        v = -1;
+      } else {
+        uint64_t U;
+        if (!(c & 1u)) {
+          const uint4 r = philox_xy((uint32_t)v, c >> 1, skc, rk);
+          ++draws;
+          U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+          spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
+        } else {
+          U = spare;
+        }
+        const uint32_t G = wc_gap(P, Jb, U);
+        if (G >= d - pos) {
+          v = -1;
+        } else {
+          u = __ldg(&g.edge[lo + pos + G].x);
+          pos += G + 1u;
+          ++c;
+          if (pos >= d) v = -1;
+        }
+      }
+    }
+    if (visit(u, lt_mask)) return;
+  }
+}
+
 __device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev, unsigned long long nv,
                                             unsigned long long dr, int lane, bool cta_tier) {
   ev = warp_sum(ev);
@@ -366,14 +436,13 @@ __device__ __forceinline__ void flush_stats(Counters* ctr, unsigned long long ev
 }
 
 // Reserve `size` pool entries (one thread).  Reservations are handed out in
-// increasing position order, so the ones that fit form a prefix ending at
-// ok_end and the rest [ok_end, cursor) are re-run by the host from fail_list.
+// increasing position order, so the ones that fit form a prefix; it ends where
+// the first one that did not fit starts (ok_end, the least such position), and
+// the rest [ok_end, cursor) are re-run by the host from fail_list.
 __device__ __forceinline__ bool reserve(const SampleJob& J, int64_t j, int size, unsigned long long* pos) {
   *pos = atomicAdd(&J.ctr->cursor, (unsigned long long)size);
-  if (*pos + (unsigned long long)size <= (unsigned long long)J.pool_cap) {
-    atomicMax(&J.ctr->ok_end, *pos + (unsigned long long)size);
-    return true;
-  }
+  if (*pos + (unsigned long long)size <= (unsigned long long)J.pool_cap) return true;
+  atomicMin(&J.ctr->ok_end, *pos);
   atomicExch(&J.ctr->pool_overflow, 1u);
   const unsigned long long f = atomicAdd(&J.ctr->fail_count, 1ull);
   J.fail_list[f] = j;
@@ -414,9 +483,10 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
     for (int i = lane; i < WT_HASH / 4; i += 32) H4[i] = make_uint4(0, 0, 0, 0);
   }
   __syncwarp();
-  // tier 0 takes the batch's samples, tier 1 the ones tier 0 handed over
+  // tier 0 takes the batch's samples (or those the lane tier listed), tier 1 the ones tier 0 handed over
   const unsigned long long count =
-      TIER == 0 ? (unsigned long long)J.count : *((volatile unsigned long long*)&J.ctr->mid_count);
+      TIER == 0 ? (J.lane_tier ? *((volatile unsigned long long*)&J.ctr->lane_count) : (unsigned long long)J.count)
+                : *((volatile unsigned long long*)&J.ctr->mid_count);
   unsigned long long* work = TIER == 0 ? &J.ctr->work : &J.ctr->mid_work;
   unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
@@ -424,7 +494,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
     if (lane == 0) idx = atomicAdd(work, 1ull);
     idx = __shfl_sync(FULL_MASK, idx, 0);
     if (idx >= count) break;
-    const int64_t j = TIER == 0 ? sample_at(J, idx) : J.mid_list[idx];
+    const int64_t j = TIER == 0 ? (J.lane_tier ? J.lane_list[idx] : sample_at(J, idx)) : J.mid_list[idx];
     const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(WC ? PURPOSE_SKIP : PURPOSE_IC, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) {
@@ -464,19 +534,21 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
     // (weighted cascade: no in-list is long, its gap walk costs the same at any degree)
     auto to_cta = [](int32_t, uint32_t, uint32_t, int) { return HEAVY_ABORT; };
     bool handoff = false;
-    while (head < tail && !overflow && !hit) {
-      const int cnt = min(32, tail - head);
-      __syncwarp();
-      const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
-      __syncwarp();
-      if constexpr (WC) {
-        expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
-      } else if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
-                 2) {
-        handoff = true;
-        break;
+    if constexpr (WC) {
+      if (!hit) wc_bfs_warp(J.g, Q, tail, J.rk, sc, lane, ev, dr, visit);
+    } else {
+      while (head < tail && !overflow && !hit) {
+        const int cnt = min(32, tail - head);
+        __syncwarp();
+        const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
+        __syncwarp();
+        if (expand_ic(J.g, v, J.rk, sc, lane, s_stage[wid], ev, dr, J.warp_heavy_groups, known, visit, to_cta) ==
+            2) {
+          handoff = true;
+          break;
+        }
+        head += cnt;
       }
-      head += cnt;
     }
     __syncwarp();
     if (handoff) {
@@ -526,20 +598,23 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
   const size_t gwarp = (size_t)blockIdx.x * WT_WARPS + wid;
   uint32_t* bits = J.wg_bitmap + gwarp * (size_t)J.bitmap_words;
   int32_t* Q = J.wg_queue + gwarp * (size_t)GQ_SLOTS;
+  // the batch's samples, or those the lane tier listed
+  const unsigned long long count =
+      J.lane_tier ? *((volatile unsigned long long*)&J.ctr->lane_count) : (unsigned long long)J.count;
   unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&J.ctr->work, 1ull);
     idx = __shfl_sync(FULL_MASK, idx, 0);
-    if (idx >= (unsigned long long)J.count) break;
-    const int64_t j = sample_at(J, idx);
+    if (idx >= count) break;
+    const int64_t j = J.lane_tier ? J.lane_list[idx] : sample_at(J, idx);
     const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_SKIP, J.stream, j));
     const int32_t root = pick_root(J, j);
     if (lane == 0) {
       atomicOr(bits + (root >> 5), 1u << (root & 31));
       Q[0] = root;
     }
-    int tail = 1, head = 0;
+    int tail = 1;
     bool overflow = false;
     bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
     __syncwarp();
@@ -560,14 +635,7 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
       if (tail > GQ_CAP) overflow = true;
       return overflow || hit;
     };
-    while (head < tail && !overflow && !hit) {
-      const int cnt = min(32, tail - head);
-      __syncwarp();
-      const int32_t v = (lane < cnt) ? Q[head + lane] : -1;
-      __syncwarp();
-      expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
-      head += cnt;
-    }
+    if (!hit) wc_bfs_warp(J.g, Q, tail, J.rk, sc, lane, ev, dr, visit);
     __syncwarp();
     if (overflow) {
       if (lane == 0) {
@@ -584,6 +652,109 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
     for (int i = lane; i < tail; i += 32) bits[Q[i] >> 5] = 0u;
     __syncwarp();
   }
+  flush_stats(J.ctr, ev, nv, dr, lane, false);
+}
+
+// Lane tier (weighted-cascade IC): one lane per sample.  Each lane runs the
+// whole BFS of its own sample with the gap walk, its queue (up to LANE_Q
+// nodes) in thread-local memory and membership tested by scanning that
+// queue.  A sample that outgrows the queue is listed in lane_list for the
+// warp tiers (its partial work is dropped).  Weighted-cascade sets are mostly
+// a handful of nodes (on the 2^25-node R-MAT graph the median is one node and
+// nine in ten have at most 18), so 32 independent samples per warp keep far
+// more memory requests in flight than one sample per warp.  Lanes claim
+// sample indices and store their sets independently of each other.
+constexpr int LANE_Q = 32;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sample_lane_wc(SampleJob J) {
+  const int lane = threadIdx.x & 31;
+  int32_t q[LANE_Q];
+  uint64_t P[31];
+  unsigned long long ev = 0, nv = 0, dr = 0;
+  for (;;) {
+    // one sample per lane; the lanes that arrive together share one atomic
+    const unsigned act = __activemask();
+    const int leader = __ffs(act) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&J.ctr->lane_work, (unsigned long long)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    const unsigned long long idx = base + (unsigned long long)__popc(act & ((1u << lane) - 1u));
+    if (idx >= (unsigned long long)J.count) break;
+    const int64_t j = sample_at(J, idx);
+    const SampleConst sc = sample_const(J.rk, (uint32_t)j, ctr_word3(PURPOSE_SKIP, J.stream, j));
+    const int32_t root = pick_root(J, j);
+    q[0] = root;
+    int tail = 1;
+    bool hit = (MODE == MODE_HIT) && test_bit(J.seed_bits, (uint32_t)root);
+    bool overflow = false;
+    for (int h = 0; h < tail && !hit && !overflow; ++h) {
+      const int32_t v = q[h];
+      const uint32_t lo = (uint32_t)__ldg(J.g.off + v);
+      const uint32_t d = (uint32_t)__ldg(J.g.off + v + 1) - lo;
+      ev += d;
+      if (d == 0u) continue;
+      const int Jb = 32 - __clz((int)d);
+      if (d >= 2u) wc_powers((0x100000000ull - wc_threshold(d)) << 32, Jb, P);
+      uint32_t pos = 0, c = 0;
+      uint64_t spare = 0;
+      while (pos < d) {
+        uint32_t e;
+        if (d == 1u) {
+          e = lo;
+          pos = 1;
+        } else {
+          uint64_t U;
+          if (!(c & 1u)) {
+            const uint4 r = philox_xy((uint32_t)v, c >> 1, sc, J.rk);
+            ++dr;
+            U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+            spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
+          } else {
+            U = spare;
+          }
+          const uint32_t G = wc_gap(P, Jb, U);
+          if (G >= d - pos) break;
+          e = lo + pos + G;
+          pos += G + 1u;
+          ++c;
+        }
+        const int32_t u = (int32_t)__ldg(&J.g.edge[e].x);
+        bool seen = false;
+        for (int i = 0; i < tail; ++i) seen |= q[i] == u;
+        if (seen) continue;
+        if (tail == LANE_Q) {
+          overflow = true;
+          break;
+        }
+        q[tail++] = u;
+        if (MODE == MODE_HIT && test_bit(J.seed_bits, (uint32_t)u)) {
+          hit = true;
+          break;
+        }
+      }
+    }
+    if (overflow) {
+      const unsigned long long b = atomicAdd(&J.ctr->lane_count, 1ull);
+      J.lane_list[b] = j;
+      continue;
+    }
+    if (MODE == MODE_STORE) {
+      unsigned long long at = 0;
+      if (reserve(J, j, tail, &at)) {
+        for (int i = 0; i < tail; ++i) {
+          J.pool_nodes[at + i] = q[i];
+          J.pool_samp[at + i] = (int32_t)j;
+        }
+        J.set_start[j] = (int64_t)at;
+        J.set_len[j] = tail;
+      }
+    } else {
+      J.hit[j - J.j0] = hit ? 1 : 0;
+    }
+    nv += (unsigned long long)tail;
+  }
+  __syncwarp();
   flush_stats(J.ctr, ev, nv, dr, lane, false);
 }
 
@@ -1026,6 +1197,11 @@ LaunchCfg sampler_config(const GraphView& g, int model, bool wc) {
   // global-bitmap warp tier (weighted-cascade IC, bitmap in global memory): 32
   // warps per SM, each with an n-bit bitmap and a GQ_SLOTS queue, or 16 where
   // the bitmaps would pass 24 GB
+  if (model == 0 && wc) {
+    int lane_per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lane_per_sm, k_sample_lane_wc<MODE_STORE>, 256, 0);
+    c.lane_blocks = c.num_sms * (lane_per_sm < 1 ? 1 : lane_per_sm);
+  }
   if (model == 0 && wc && !c.cta_smem_bitmap) {
     const double per_block = (double)words * 4.0 * WT_WARPS;
     c.wg_blocks = c.num_sms * ((double)c.num_sms * 4 * per_block <= 24e9 ? 4 : 2);
@@ -1055,6 +1231,10 @@ static void launch_warp_ic(const SampleJob& J, const LaunchCfg& c, cudaStream_t 
 
 cudaError_t launch_sample_warp(const SampleJob& J, const LaunchCfg& c, cudaStream_t st) {
   const dim3 grid(c.warp_blocks), block(WT_WARPS * 32);
+  if (J.model == 0 && J.wc_implicit && J.lane_tier) {
+    if (J.mode == MODE_STORE) k_sample_lane_wc<MODE_STORE><<<c.lane_blocks, 256, 0, st>>>(J);
+    else k_sample_lane_wc<MODE_HIT><<<c.lane_blocks, 256, 0, st>>>(J);
+  }
   if (J.model == 0 && J.wc_implicit && J.warp_global && c.wg_blocks > 0) {
     if (J.mode == MODE_STORE) k_sample_warp_wcg<MODE_STORE><<<c.wg_blocks, block, 0, st>>>(J);
     else k_sample_warp_wcg<MODE_HIT><<<c.wg_blocks, block, 0, st>>>(J);

@@ -2,6 +2,8 @@
 same seeded inputs, bit-exact for every integer result (CSR, thresholds, RR
 sets, counts, seed sets, coverage, Estimate-Inf T, round traces) and exactly
 equal FP64 influence (the 1e-12 relative bound is the stated tolerance)."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -300,14 +302,16 @@ def test_wc_cta_tier_sets(scale, m_draw, small_q):
     # Stored sets and hit-test mode both equal the oracle.
     # On the 2^21-node graph the global-bitmap warp tier (one warp per sample of
     # any size up to 2^16 nodes, visited bits in global memory) takes every
-    # sample in the last two configurations, the second handing samples that
-    # meet a long in-list on to the CTA tier.
+    # sample in the last two configurations.  Each configuration runs with the
+    # lane tier first (sets of up to 32 nodes end there) and without it.
     el = inputs.rmat(scale, m_draw, seed=7)
     og, gg = _pair(el)
     P.ssa_set_queue_tuning(gg, small_q)
-    for mid, heavy, wg in ((0, 64, 0), (0, 0x7FFFFFFF, 0), (16384, 64, 0), (0, 0x7FFFFFFF, 1), (0, 64, 1)):
+    for (mid, heavy, wg), lane in itertools.product(
+            ((0, 64, 0), (0, 0x7FFFFFFF, 0), (16384, 64, 0), (0, 0x7FFFFFFF, 1), (0, 64, 1)), (0, 1)):
         P.ssa_set_tuning(gg, mid, heavy)
         P.ssa_set_warp_tier(gg, wg)
+        P.ssa_set_lane_tier(gg, lane)
         op, gp = _check_pool(og, gg, oracle.IC, seed=5, stream=0, N=2000)
         seeds, _, _ = op.max_coverage(2000, 4)
         for lam in (15.5, 400.0):
@@ -318,6 +322,7 @@ def test_wc_cta_tier_sets(scale, m_draw, small_q):
         assert np.diff(off).max() > small_q  # the full-size stage was needed
     P.ssa_set_queue_tuning(gg, 0)
     P.ssa_set_warp_tier(gg, 0)
+    P.ssa_set_lane_tier(gg, 1)
 
 
 def test_autotune_picks_a_candidate():
