@@ -168,7 +168,8 @@ ssa_status ssa_set_queue_tuning(const ssa_graph* g, int32_t small_queue);
 /* Weighted-cascade IC on graphs whose n-bit bitmap does not fit shared memory
  * (n/8 above 192 KB): with global_bitmap = 1 every sample is built by one warp
  * whose visited set is its own n-bit bitmap in global memory and whose queue
- * holds up to 2^16 nodes; larger sets go to the CTA tier.  0 (the default)
+ * holds up to 2^16 nodes (up to mid_cap of ssa_set_tuning when that is
+ * nonzero); larger sets go to the CTA tier.  0 (the default)
  * keeps the hash warp tiers of ssa_set_tuning.  ssa_autotune times this tier
  * where it exists.  Results never depend on it. */
 ssa_status ssa_set_warp_tier(const ssa_graph* g, int32_t global_bitmap);

@@ -104,6 +104,8 @@ struct ssa_graph {
   int weighting = 0;
   int64_t* off = nullptr;
   uint2* edge = nullptr;
+  uint64_t* wc_pow = nullptr;  // weighted cascade: gap powers per in-degree (build_wc_pow)
+  int wc_pow_k = 0;
   int64_t bytes = 0;
   // IC sampler hand-over sizes chosen by the autotuner (-1: not tuned yet)
   mutable std::mutex tune_mu;
@@ -118,6 +120,8 @@ struct ssa_graph {
     v.m = m;
     v.off = off;
     v.edge = edge;
+    v.wc_pow = wc_pow;
+    v.wc_pow_k = wc_pow_k;
     return v;
   }
 };
@@ -467,15 +471,20 @@ struct Sampler {
   }
 
   // Append samples [pool.count, pool.count + count) of (seed, stream) to the pool.
-  // The pool is sized from the mean set size seen so far (a 1024-sample pilot
-  // batch measures it when the pool is empty); samples whose reservation still
-  // does not fit are listed by the kernels and re-run after the pool grows, so
-  // no finished set is sampled twice.
-  ssa_status append(DevPool& P, uint64_t seed, uint32_t stream, int64_t count, Exec& X) {
+  // The pool is sized from the mean set size seen so far (a pilot batch of up
+  // to 8192 samples measures it when the pool is empty); samples whose
+  // reservation still does not fit are listed by the kernels and re-run after
+  // the pool grows, so no finished set is sampled twice.  The ones that miss
+  // are the last to finish, the largest sets, so an estimate that runs short
+  // re-runs the most expensive samples: set sizes are heavy-tailed (under
+  // weighted cascade the mean of 512 samples is often a quarter off), hence
+  // the large pilot and a wider margin while the mean rests on few samples.
+  ssa_status append(DevPool& P, uint64_t seed, uint32_t stream, int64_t count, Exec& X, bool pilot_first = true) {
     if (count <= 0) return SSA_OK;
-    if (P.count == 0 && count > 1024) {
-      const int64_t pilot = std::min<int64_t>(512, count / 4);
-      TRY(append(P, seed, stream, pilot, X));
+    if (pilot_first && P.count == 0 && count > 1024) {
+      // one pilot batch: each batch ends with its slowest sample, so a chain of them costs a tail each
+      const int64_t pilot = std::min<int64_t>(8192, count / 4);
+      TRY(append(P, seed, stream, pilot, X, false));
       count -= pilot;
     }
     const int64_t j0 = P.count;
@@ -494,7 +503,8 @@ struct Sampler {
       P.cap_sets = want;
     }
     const double mean = P.count > 0 ? (double)P.entries / (double)P.count : 16.0;
-    int64_t want = P.entries + (int64_t)(mean * (double)count * 1.15) + 65536;
+    const double margin = P.count >= 65536 ? 1.15 : 1.5;
+    int64_t want = P.entries + (int64_t)(mean * (double)count * margin) + 65536;
     TRY(grow_entries(P, want, X));
     int64_t todo = count;
     const int64_t* list = nullptr;
@@ -1249,6 +1259,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
   std::vector<int64_t> gains((size_t)k);
   int32_t t = 0;
   int64_t extra_rr = 0;
+  int64_t used = 0;  // SSA: sets of the last round (the pool may hold more, sampled ahead)
   double influence = 0.0;
   const bool graphs = sv->use_graphs && !X.timing;
   // Max-Coverage over the whole batches [0, N), and for D-SSA the stare count
@@ -1320,7 +1331,16 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
         rec.eps1 = P.eps1;
         rec.eps2 = P.eps2;
         rec.eps3 = P.eps3;
-        if ((st = S.append(pool, p->seed, 0, N - pool.count, X)) != SSA_OK) break;
+        if (pool.count < N) {
+          // Each batch ends with its slowest sample (one warp walking the batch's
+          // largest set), a fixed cost that dominates small batches.  So the pool
+          // grows by at least `ahead` sets: the first rounds then read prefixes
+          // of one batch.  Sets are keyed by sample id, so round t still sees
+          // exactly R_t = samples [0, N); the extra samples serve the next rounds.
+          const int64_t ahead = std::min<int64_t>(n / 64, 131072);
+          if ((st = S.append(pool, p->seed, 0, std::max<int64_t>(N - pool.count, ahead), X)) != SSA_OK) break;
+        }
+        used = N;
         int64_t cov = 0;
         if ((st = greedy_round(N, &cov, nullptr)) != SSA_OK) break;
         rec.cov = cov;
@@ -1389,7 +1409,7 @@ ssa_status solve_impl(ssa_solver* sv, const ssa_params* p, ssa_result* out) {
     std::memcpy(out->seeds, seeds.data(), sizeof(int32_t) * (size_t)k);
     out->influence = influence;
     out->rounds = t;
-    out->n_rr = pool.count + extra_rr;
+    out->n_rr = (dssa ? pool.count : used) + extra_rr;
     out->pool_entries = pool.entries;
     out->edge_visits = S.edge_visits;
     out->node_visits = S.node_visits;
@@ -1512,7 +1532,18 @@ ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_
       rc = fail(SSA_E_CUDA, "graph build: %s", cudaGetErrorString(e));
       break;
     }
-    if (herr) rc = fail(SSA_E_ARG, "edge endpoint outside [0, n)");
+    if (herr) {
+      rc = fail(SSA_E_ARG, "edge endpoint outside [0, n)");
+      break;
+    }
+    if (weighting == SSA_W_WC) {
+      e = build_wc_pow(g->off, n, &g->wc_pow, &g->wc_pow_k, st);
+      if (e != cudaSuccess) {
+        rc = fail(e == cudaErrorMemoryAllocation ? SSA_E_NOMEM : SSA_E_CUDA, "power table: %s", cudaGetErrorString(e));
+        break;
+      }
+      if (g->wc_pow_k > 0) g->bytes += (int64_t)(sizeof(uint64_t) * (((size_t)g->wc_pow_k - 1) << g->wc_pow_k) + 8);
+    }
   } while (false);
   if (d_src) cudaFreeAsync(d_src, st);
   if (d_dst) cudaFreeAsync(d_dst, st);
@@ -1523,6 +1554,7 @@ ssa_status ssa_load_graph(int64_t n, int64_t m, const int32_t* src, const int32_
   if (rc != SSA_OK) {
     if (g->off) cudaFree(g->off);
     if (g->edge) cudaFree(g->edge);
+    if (g->wc_pow) cudaFree(g->wc_pow);
     delete g;
     return rc;
   }
@@ -1559,18 +1591,21 @@ ssa_status ssa_gen_rmat(int32_t scale, int64_t m_draw, double a, double b, doubl
   int64_t m = 0;
   cudaError_t e = rmat_graph(scale, m_draw, prob_threshold(a), prob_threshold(a + b), prob_threshold(a + b + c), seed,
                              (int)weighting, weight_seed, &m, &g->off, &g->edge, st, &launches);
+  if (e == cudaSuccess && weighting == SSA_W_WC) e = build_wc_pow(g->off, g->n, &g->wc_pow, &g->wc_pow_k, st);
   const cudaError_t e2 = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) {
     if (g->off) cudaFree(g->off);
     if (g->edge) cudaFree(g->edge);
+    if (g->wc_pow) cudaFree(g->wc_pow);
     delete g;
     return fail(e == cudaErrorMemoryAllocation ? SSA_E_NOMEM : SSA_E_CUDA, "R-MAT generation: %s",
                 cudaGetErrorString(e));
   }
   g->m = m;
   g->bytes = (int64_t)(sizeof(int64_t) * (size_t)(g->n + 1) + sizeof(uint2) * (size_t)(((m + 3) / 4) * 4 + 4));
+  if (g->wc_pow_k > 0) g->bytes += (int64_t)(sizeof(uint64_t) * (((size_t)g->wc_pow_k - 1) << g->wc_pow_k) + 8);
   *out = g;
   return SSA_OK;
 }
@@ -1580,6 +1615,7 @@ ssa_status ssa_free_graph(ssa_graph* g) {
   cudaDeviceSynchronize();
   if (g->off) cudaFree(g->off);
   if (g->edge) cudaFree(g->edge);
+  if (g->wc_pow) cudaFree(g->wc_pow);
   delete g;
   return SSA_OK;
 }

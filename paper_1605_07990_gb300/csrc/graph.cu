@@ -221,4 +221,62 @@ cudaError_t build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_
   return e;
 }
 
+namespace {
+__global__ void k_max_in_degree(const int64_t* off, int64_t n, unsigned long long* out) {
+  unsigned long long best = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long d = (unsigned long long)(off[v + 1] - off[v]);
+    best = d > best ? d : best;
+  }
+  for (int s = 16; s; s >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, s);
+    best = o > best ? o : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
+// Row of in-degree d (1 <= d < 2^K): the powers q^(2^i), i < bit length of d,
+// of the weighted-cascade gap form (Q = (2^32 - t) << 32 with t = floor(2^32/d),
+// 0xFFFFFFFF for d = 1; each power the high 64 bits of the previous one squared).
+__global__ void k_wc_pow_rows(uint64_t* tab, int K) {
+  const int64_t rows = int64_t(1) << K;
+  for (int64_t d = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < rows;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    const int k = 63 - __clzll(d);
+    const uint64_t base = k == 0 ? 0ull : (uint64_t)(k - 1) * (1ull << k) + 1ull;
+    uint64_t* row = tab + base + (uint64_t)(d - (int64_t(1) << k)) * (uint64_t)(k + 1);
+    const uint32_t t = d == 1 ? 0xFFFFFFFFu : (uint32_t)(0x100000000ull / (uint64_t)d);
+    uint64_t p = (0x100000000ull - t) << 32;
+    for (int i = 0; i <= k; ++i) {
+      row[i] = p;
+      p = __umul64hi(p, p);
+    }
+  }
+}
+}  // namespace
+
+cudaError_t build_wc_pow(const int64_t* d_off, int64_t n, uint64_t** tab, int* k_out, cudaStream_t st) {
+  *tab = nullptr;
+  *k_out = 0;
+  unsigned long long* d_max = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_max), sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  unsigned long long maxd = 0;
+  cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), st);
+  k_max_in_degree<<<grid_for(n, 256), 256, 0, st>>>(d_off, n, d_max);
+  cudaMemcpyAsync(&maxd, d_max, sizeof(maxd), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  cudaFree(d_max);
+  if (e != cudaSuccess) return e;
+  int K = 0;
+  while (K < WC_POW_K && (1ull << K) <= maxd) ++K;  // rows for every d < 2^K that occurs
+  if (K < 2) return cudaSuccess;                     // no in-list of 2 or more edges
+  const size_t entries = (size_t)(K - 1) * ((size_t)1 << K) + 1;
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(tab), sizeof(uint64_t) * entries, st)) != cudaSuccess) return e;
+  k_wc_pow_rows<<<grid_for((int64_t)1 << K, 256), 256, 0, st>>>(*tab, K);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  *k_out = K;
+  return cudaSuccess;
+}
+
 }  // namespace ssa

@@ -16,7 +16,19 @@ struct GraphView {
   int64_t n = 0, m = 0;
   const int64_t* off = nullptr;  // n+1
   const uint2* edge = nullptr;   // m rounded up to a multiple of 4 (+4): {src, thr}
+  // weighted cascade: the gap form's powers q^(2^i) of every in-degree d < 2^wc_pow_k
+  // (rows of bit-length entries, in order of d; null / 0 for other weightings)
+  const uint64_t* wc_pow = nullptr;
+  int wc_pow_k = 0;
 };
+
+// In-degrees of up to 2^WC_POW_K - 1 take their gap powers from the graph's
+// table ((WC_POW_K - 1) 2^WC_POW_K + 1 entries, 160 MB); larger ones build them.
+constexpr int WC_POW_K = 20;
+
+// The weighted-cascade power table of a CSR (rows for every in-degree below
+// min(2^WC_POW_K, 2 * max in-degree)); *tab stays null when no in-list has 2 edges.
+cudaError_t build_wc_pow(const int64_t* d_off, int64_t n, uint64_t** tab, int* k, cudaStream_t st);
 
 // Device counters of one sampling batch.
 // Bounded waits of the weighted-cascade CTA tier that gave up (Counters::error).

@@ -275,6 +275,18 @@ __device__ __forceinline__ void wc_powers(uint64_t Q, int J, uint64_t* P) {
   }
 }
 
+// The powers of in-degree d >= 2: the graph's table row when d < 2^wc_pow_k
+// (rows for d in [2^k, 2^(k+1)) hold k+1 entries and follow all shorter rows,
+// so row d starts at (k-1) 2^k + 1 + (d - 2^k)(k+1)), else built into `own`.
+__device__ __forceinline__ const uint64_t* wc_power_row(const GraphView& g, uint32_t d, int J, uint64_t* own) {
+  if (d < (1u << g.wc_pow_k)) {
+    const int k = J - 1;
+    return g.wc_pow + ((uint64_t)(k - 1) << k) + 1ull + (uint64_t)(d - (1u << k)) * (uint64_t)J;
+  }
+  wc_powers((0x100000000ull - wc_threshold(d)) << 32, J, own);
+  return own;
+}
+
 __device__ __forceinline__ uint32_t wc_gap(const uint64_t* P, int J, uint64_t U) {
   uint64_t A = 0;
   bool first = true;
@@ -308,8 +320,8 @@ __device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const u
   }
   ev += d;
   const int J = 32 - __clz((int)d);
-  uint64_t P[31];  // q^(2^i), i < J (per lane; J <= 31 as d < 2^31)
-  if (d >= 2u) wc_powers((0x100000000ull - wc_threshold(d)) << 32, J, P);
+  uint64_t own[31];  // q^(2^i), i < J, when the graph's table has no row for d
+  const uint64_t* P = d >= 2u ? wc_power_row(g, d, J, own) : nullptr;
   uint32_t pos = 0, c = 0;
   uint64_t spare = 0;
   bool active = d > 0u;
@@ -367,7 +379,8 @@ __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q
   uint32_t lo = 0, d = 0, pos = 0, c = 0;
   int Jb = 0;
   uint64_t spare = 0;
-  uint64_t P[31];  // q^(2^i), i < Jb, of the lane's node
+  uint64_t own[31];  // q^(2^i), i < Jb, of the lane's node when the graph's table has no row for it
+  const uint64_t* P = nullptr;
   for (;;) {
     __syncwarp();  // queue entries written by other lanes in the last round
     const bool need = v < 0;
@@ -383,7 +396,7 @@ __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q
         pos = 0;
         c = 0;
         Jb = 32 - __clz((int)d);
-        if (d >= 2u) wc_powers((0x100000000ull - wc_threshold(d)) << 32, Jb, P);
+        if (d >= 2u) P = wc_power_row(g, d, Jb, own);
       }
     }
     head += take;
@@ -584,10 +597,10 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_ic(SampleJob J
   flush_stats(J.ctr, ev, nv, dr, lane, false);
 }
 
-// Weighted-cascade IC, one warp per sample of up to GQ_CAP nodes, with the
-// visited set as a per-warp n-bit bitmap in global memory and the BFS queue in
-// global memory: one tier for every set size up to the queue, where the
-// hash tiers stop at 512 and 16384 nodes.  Sets that outgrow the queue go to
+// Weighted-cascade IC, one warp per sample of up to GQ_CAP nodes (or mid_cap,
+// when set), with the visited set as a per-warp n-bit bitmap in global memory
+// and the BFS queue in global memory: one tier for every set size up to the
+// queue, where the hash tiers stop at 512 and 16384 nodes.  Larger sets go to
 // the CTA tier.
 constexpr int GQ_CAP = 1 << 16;
 constexpr int GQ_SLOTS = GQ_CAP + 32;  // room for one round past the cap
@@ -601,6 +614,8 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
   // the batch's samples, or those the lane tier listed
   const unsigned long long count =
       J.lane_tier ? *((volatile unsigned long long*)&J.ctr->lane_count) : (unsigned long long)J.count;
+  // sets above mid_cap nodes (when set) go on to the CTA tier, whose warps share a sample
+  const int cap = J.mid_cap > 0 ? min(J.mid_cap, GQ_CAP) : GQ_CAP;
   unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
     unsigned long long idx = 0;
@@ -627,12 +642,12 @@ __global__ void __launch_bounds__(WT_WARPS * 32, 4) k_sample_warp_wcg(SampleJob 
       const unsigned m = __ballot_sync(FULL_MASK, is_new);
       bool h = false;
       if (is_new) {
-        Q[tail + __popc(m & lt_mask)] = (int32_t)u;  // tail <= GQ_CAP before this round: fits GQ_SLOTS
+        Q[tail + __popc(m & lt_mask)] = (int32_t)u;  // tail <= cap <= GQ_CAP before this round: fits GQ_SLOTS
         if (MODE == MODE_HIT) h = test_bit(J.seed_bits, u);
       }
       tail += __popc(m);
       if (MODE == MODE_HIT) hit = __any_sync(FULL_MASK, h) || hit;
-      if (tail > GQ_CAP) overflow = true;
+      if (tail > cap) overflow = true;
       return overflow || hit;
     };
     if (!hit) wc_bfs_warp(J.g, Q, tail, J.rk, sc, lane, ev, dr, visit);
@@ -670,7 +685,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_sample_lane_wc(SampleJob J) {
   const int lane = threadIdx.x & 31;
   int32_t q[LANE_Q];
-  uint64_t P[31];
+  uint64_t own[31];  // powers of a node whose in-degree has no row in the graph's table
   unsigned long long ev = 0, nv = 0, dr = 0;
   for (;;) {
     // one sample per lane; the lanes that arrive together share one atomic
@@ -695,7 +710,7 @@ __global__ void __launch_bounds__(256) k_sample_lane_wc(SampleJob J) {
       ev += d;
       if (d == 0u) continue;
       const int Jb = 32 - __clz((int)d);
-      if (d >= 2u) wc_powers((0x100000000ull - wc_threshold(d)) << 32, Jb, P);
+      const uint64_t* P = d >= 2u ? wc_power_row(J.g, d, Jb, own) : nullptr;
       uint32_t pos = 0, c = 0;
       uint64_t spare = 0;
       while (pos < d) {

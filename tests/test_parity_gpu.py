@@ -325,6 +325,32 @@ def test_wc_cta_tier_sets(scale, m_draw, small_q):
     P.ssa_set_lane_tier(gg, 1)
 
 
+def test_wc_hubs_inside_and_beyond_power_table():
+    # Weighted cascade reads the gap powers of in-degrees below 2^20 from the
+    # graph's table and builds those of longer in-lists itself.  Two stars feed
+    # a root node: hub 1 with 2^20 - 1 in-edges (the table's last row) and hub 2
+    # with 2^20 + 3 (beyond it); the root (node 0) is every set's source
+    # (WRIS), and its in-list {1, 2} reaches both hubs.  Stored sets in every
+    # tier (lane tier on and off) and hit-test counts equal the oracle.
+    d1, d2 = (1 << 20) - 1, (1 << 20) + 3
+    n = 3 + d1 + d2
+    src = np.concatenate([[1, 2], np.arange(3, 3 + d1), np.arange(3 + d1, n)]).astype(np.int32)
+    dst = np.concatenate([[0, 0], np.full(d1, 1), np.full(d2, 2)]).astype(np.int32)
+    el = inputs.EdgeList(n, src, dst)
+    og, gg = _pair(el)
+    benefit = np.zeros(n, dtype=np.int64)
+    benefit[0] = 1
+    for lane in (1, 0):
+        P.ssa_set_lane_tier(gg, lane)
+        op, gp = _check_pool(og, gg, oracle.IC, seed=8, stream=0, N=3000, benefit=benefit)
+    sizes = np.diff(op.arrays()[0])
+    assert sizes.max() >= 3  # some sets reach a hub and take a live edge of its long in-list
+    seeds = np.array([3 + d1 // 2, 3 + d1 + d2 // 2], np.int32)
+    assert P.ssa_estimate_inf(gg, oracle.IC, 8, 1, seeds, 5.5, 4000, benefit=benefit) == \
+        oracle.estimate_inf(og, oracle.IC, 8, 1, seeds, 5.5, 4000, benefit=benefit)[:2]
+    P.ssa_set_lane_tier(gg, 1)
+
+
 def test_autotune_picks_a_candidate():
     el = c1_edges()
     gg = P.ssa_load_graph(el.n, el.src, el.dst)
