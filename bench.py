@@ -67,7 +67,13 @@ PHILOX_MIN_INSTR = 40
 # class, valid only for the kernel sources they were taken on (hash of
 # csrc/sample.cu, csrc/device.cuh, csrc/kernels.h); any other build reports
 # traffic null.
-TRAFFIC = {}
+TRAFFIC = {
+    # 2^23-node capture (profiles/sample_warp_wcg_wc_ic_rmat23.md): 14.14 GB of DRAM traffic over
+    # 47,589,152 node visits for the lane and warp tiers of a 2M-set grow, scaled to the 2^25-node
+    # workload by its node visits (the traffic is four to five random sector touches per visit)
+    ("ssa_ic_wc_rmat25_m1.3G_k100", "sample_warp"): {"src": "2668410468aba68a", "bytes_per_node_visit": 297.2},
+    ("ssa_ic_wc_rmat23_m128M_k100", "sample_warp"): {"src": "2668410468aba68a", "bytes_per_node_visit": 297.2},
+}
 
 
 def kernel_source_hash() -> str:
@@ -600,8 +606,9 @@ def main():
     if args.e2e_steps > 0:
         line["e2e"] = {"value": rr_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(el.m * 8),
                        "d2h_bytes_per_step": int(k * 4 + 64), "steps": args.e2e_steps,
-                       "includes": "graph upload + device CSR build + solve (first solve on a new graph handle "
-                                   "runs the sampler autotuner) + seeds to host",
+                       "includes": "graph upload + device CSR build (and, under weighted cascade, the gap-power "
+                                   "table) + solve (the first solve on a new graph handle picks the sampler tiers) "
+                                   "+ seeds to host",
                        "load_s_per_step": t_load / args.e2e_steps, "solve_s_per_step": t_solve / args.e2e_steps,
                        "seeds": "the first e2e steps use the timed steps' Philox seeds"}
 

@@ -23,24 +23,36 @@ namespace {
 constexpr int TPB = 256;
 
 // samp == nullptr: every entry in [e0, e1) counts; else only samples in [jlo, jhi)
+// Index build.  Hubs appear in a large share of the sets, so the lanes of a
+// warp that hold the same node are grouped (labeled_partition) and one of
+// them issues the group's atomic: one atomic per distinct node per warp
+// instead of one per entry on the hub's counter.
 __global__ void k_count_nodes(const int32_t* __restrict__ nodes, const int32_t* __restrict__ samp, int64_t e0,
                               int64_t e1, int64_t jlo, int64_t jhi, int32_t* cnt) {
+  namespace cg = cooperative_groups;
   for (int64_t q = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < e1; q += (int64_t)gridDim.x * blockDim.x) {
     if (samp) {
       const int64_t s = samp[q];
       if (s < jlo || s >= jhi) continue;
     }
-    atomicAdd(cnt + nodes[q], 1);
+    const int32_t v = nodes[q];
+    const cg::coalesced_group same = cg::labeled_partition(cg::coalesced_threads(), v);
+    if (same.thread_rank() == 0) atomicAdd(cnt + v, (int)same.size());
   }
 }
 
 __global__ void k_scatter_index(const int32_t* __restrict__ nodes, const int32_t* __restrict__ samp, int64_t e0,
                                 int64_t e1, int64_t jlo, int64_t jhi, unsigned long long* cur, int32_t* inv_samp) {
+  namespace cg = cooperative_groups;
   for (int64_t q = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < e1;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = samp[q];
     if (s < jlo || s >= jhi) continue;
-    const unsigned long long pos = atomicAdd(cur + nodes[q], 1ull);
+    const int32_t v = nodes[q];
+    const cg::coalesced_group same = cg::labeled_partition(cg::coalesced_threads(), v);
+    unsigned long long pos = 0;
+    if (same.thread_rank() == 0) pos = atomicAdd(cur + v, (unsigned long long)same.size());
+    pos = same.shfl(pos, 0) + same.thread_rank();
     inv_samp[pos] = s;
   }
 }
