@@ -61,7 +61,6 @@ def _load():
     sig = {
         "orc_philox4x32_10": (None, [vp, vp, vp]),
         "orc_wc_gap": (u32, [i64, u64]),
-        "orc_gap_run": (u32, [u32, i64, u64]),
         "orc_graph_build": (vp, [i64, i64, vp, vp, C.c_int, vp, u64]),
         "orc_graph_free": (None, [vp]),
         "orc_graph_off": (vp, [vp]), "orc_graph_src": (vp, [vp]), "orc_graph_thr": (vp, [vp]),
@@ -95,12 +94,6 @@ def wc_gap(d: int, U: int) -> int:
     """Dead-edge run before the next live one in a weighted-cascade in-list of
     d edges, for the 64-bit uniform U (the gap form of oracle.c)."""
     return int(_load().orc_wc_gap(d, U & 0xFFFFFFFFFFFFFFFF))
-
-
-def gap_run(t: int, length: int, U: int) -> int:
-    """Dead-edge run before the next live one in a run of `length` edges that
-    are live with probability t / 2^32 each (the gap form of oracle.c)."""
-    return int(_load().orc_gap_run(t, length, U & 0xFFFFFFFFFFFFFFFF))
 
 
 def _p(a):

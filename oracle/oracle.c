@@ -17,10 +17,8 @@
  *     threshold; 0xFFFFFFFF means probability exactly 1.
  *   - RR set (Definition 2): random source v, random sample graph g, the nodes
  *     that reach v in g.  IC (Sec. 2.1): each edge is live independently with
- *     probability w; under weighted-cascade and trivalency weights the live
- *     in-edges of a node are drawn as geometric gaps over runs of equal
- *     probability (the same law; see "gap form" below).  Trivalency in-lists
- *     are grouped by class so that each class is one run.
+ *     probability w; under weighted-cascade weights the live in-edges of a
+ *     node are drawn as geometric gaps (the same law; see "gap form" below).
  *     LT (Sec. 2.1) in its live-edge form: each node keeps at most one
  *     in-edge, (u,v) with probability w(u,v).
  *   - WRIS (Sec. 6.3.1): the source is drawn proportionally to node benefit.
@@ -159,23 +157,6 @@ orc_graph* orc_graph_build(int64_t n, int64_t m, const int32_t* src, const int32
       g->thr[e] = t;
     }
   }
-  if (weighting == W_TRIVALENCY) {
-    /* Each in-list is regrouped by probability class (0.1, then 0.01, then
-     * 0.001), keeping the (src, input position) order inside a class: the IC
-     * sampler walks each class's run of edges by geometric gaps.  The class
-     * of an edge stays the WEIGHT draw of its (dst, src, position) rank. */
-    int32_t* tsrc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m ? m : 1));
-    uint32_t* tthr = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
-    for (int64_t v = 0; v < n; ++v) {
-      int64_t w = g->off[v];
-      for (int c = 0; c < 3; ++c)
-        for (int64_t e = g->off[v]; e < g->off[v + 1]; ++e)
-          if (g->thr[e] == TRIVALENCY_THR[c]) { tsrc[w] = g->src[e]; tthr[w] = g->thr[e]; ++w; }
-    }
-    memcpy(g->src, tsrc, sizeof(int32_t) * (size_t)m);
-    memcpy(g->thr, tthr, sizeof(uint32_t) * (size_t)m);
-    free(tsrc); free(tthr);
-  }
   free(cnt); free(by_src); free(order);
   return g;
 }
@@ -206,22 +187,17 @@ int64_t orc_graph_m(const orc_graph* g) { return g->m; }
 /* below 2^-50 at every threshold; pinned against exact powers in the tests). */
 /* The walk: pos = 0, gap c = 0, 1, ...: G = G(U_c); stop when G >= d - pos;  */
 /* else edge off[v] + pos + G is live and pos moves past it.                   */
-/* Trivalency: the same walk over each class's run of v's in-list (class k =  */
-/* 0, 1, 2 for 0.1, 0.01, 0.001), with that class's t, J the run's bit length */
-/* and the draws keyed by (v, k, c).  The truncated powers are within an      */
-/* absolute 2^(J-64) of q^(2^i): gaps whose survival q^g falls below about    */
-/* 2^-64 are cut off (for p = 0.1 past g ~ 416), a law change below 2^-64.    */
 /* ------------------------------------------------------------------------ */
 static uint64_t mulq(uint64_t a, uint64_t b) {
   return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
 }
 
-/* G(U) for a run of len edges that are live with probability t/2^32 each
- * (q = (2^32 - t) << 32); J = bit length of len. */
-static uint32_t gap_run(uint32_t t, int64_t len, uint64_t U) {
+uint32_t orc_wc_gap(int64_t d, uint64_t U) {
+  if (d < 2 || d > 0x7FFFFFFF) return 0;
+  uint32_t t = (uint32_t)((UINT64_C(1) << 32) / (uint64_t)d);
   uint64_t q = ((UINT64_C(1) << 32) - t) << 32;
   int J = 0;
-  while ((INT64_C(1) << J) <= len) ++J;  /* 2^J > len */
+  while ((INT64_C(1) << J) <= d) ++J;  /* 2^J > d */
   uint64_t P[32];
   P[0] = q;
   for (int i = 1; i < J; ++i) P[i] = mulq(P[i - 1], P[i - 1]);
@@ -235,20 +211,10 @@ static uint32_t gap_run(uint32_t t, int64_t len, uint64_t U) {
   return g;
 }
 
-uint32_t orc_wc_gap(int64_t d, uint64_t U) {
-  if (d < 2 || d > 0x7FFFFFFF) return 0;
-  return gap_run((uint32_t)((UINT64_C(1) << 32) / (uint64_t)d), d, U);
-}
-
-uint32_t orc_gap_run(uint32_t t, int64_t len, uint64_t U) {
-  if (len < 1 || len > 0x7FFFFFFF || t == 0u || t == 0xFFFFFFFFu) return 0;
-  return gap_run(t, len, U);
-}
-
-/* the 64-bit uniform of gap c of class run k (0 for weighted cascade) of node v in sample j */
-static uint64_t skip_uniform(uint64_t seed, uint32_t stream, uint64_t j, int32_t v, uint32_t k, uint64_t c) {
+/* the 64-bit uniform of gap c of node v in sample j */
+static uint64_t skip_uniform(uint64_t seed, uint32_t stream, uint64_t j, int32_t v, uint64_t c) {
   uint32_t r[4];
-  keyed(seed, P_SKIP, stream, j, (uint64_t)(uint32_t)v | ((((uint64_t)k << 30) | (c >> 1)) << 32), r);
+  keyed(seed, P_SKIP, stream, j, (uint64_t)(uint32_t)v | ((c >> 1) << 32), r);
   unsigned w = 2u * (unsigned)(c & 1u);
   return (uint64_t)r[w] | ((uint64_t)r[w + 1] << 32);
 }
@@ -311,43 +277,27 @@ static int64_t rr_set(orc_sampler* s, uint32_t stream, uint64_t j, int32_t* out)
   int64_t size = 0;
   s->queue[size++] = root;
   s->visited[root] = 1;
-  if (s->model == MODEL_IC && (g->weighting == W_WC || g->weighting == W_TRIVALENCY)) {
-    /* reverse BFS; the live in-edges of each node by the gap walk above, run
-     * by run: weighted cascade has one run (the whole in-list), trivalency
-     * one per class present (the in-list is grouped by class) */
+  if (s->model == MODEL_IC && g->weighting == W_WC) {
+    /* reverse BFS; the live in-edges of each node by the gap walk above */
     for (int64_t head = 0; head < size; ++head) {
       int32_t v = s->queue[head];
       int64_t lo = g->off[v], d = g->off[v + 1] - lo;
       s->edge_visits += d;
-      for (int k = 0; k < (g->weighting == W_WC ? 1 : 3); ++k) {
-        int64_t rlo = lo, len = d;
-        uint32_t t;
-        if (g->weighting == W_WC) {
-          t = d == 1 ? 0xFFFFFFFFu : (d >= 2 ? (uint32_t)((UINT64_C(1) << 32) / (uint64_t)d) : 0u);
+      int64_t pos = 0;
+      for (uint64_t c = 0; pos < d; ++c) {
+        int64_t e;
+        if (d == 1) {
+          e = lo;
+          pos = 1;
         } else {
-          /* the run of class k: the edges of v with threshold TRIVALENCY_THR[k] */
-          t = TRIVALENCY_THR[k];
-          rlo = lo;
-          while (rlo < lo + d && g->thr[rlo] != t) ++rlo;
-          len = 0;
-          while (rlo + len < lo + d && g->thr[rlo + len] == t) ++len;
+          uint32_t G = orc_wc_gap(d, skip_uniform(s->seed, stream, j, v, c));
+          if ((int64_t)G >= d - pos) break;
+          e = lo + pos + G;
+          pos += (int64_t)G + 1;
         }
-        int64_t pos = 0;
-        for (uint64_t c = 0; pos < len; ++c) {
-          int64_t e;
-          if (t == 0xFFFFFFFFu) {
-            e = rlo + pos;  /* probability 1: every edge (weighted cascade, d = 1) */
-            pos += 1;
-          } else {
-            uint32_t G = gap_run(t, len, skip_uniform(s->seed, stream, j, v, (uint32_t)k, c));
-            if ((int64_t)G >= len - pos) break;
-            e = rlo + pos + G;
-            pos += (int64_t)G + 1;
-          }
-          if (!s->visited[g->src[e]]) {
-            s->visited[g->src[e]] = 1;
-            s->queue[size++] = g->src[e];
-          }
+        if (!s->visited[g->src[e]]) {
+          s->visited[g->src[e]] = 1;
+          s->queue[size++] = g->src[e];
         }
       }
     }
