@@ -302,73 +302,107 @@ __device__ __forceinline__ uint32_t wc_gap(const uint64_t* P, int J, uint64_t U)
   return gap;
 }
 
-// Weighted-cascade IC expansion of up to 32 frontier nodes, one per lane
-// (v = -1 for none).  Each lane walks its node's in-list [lo, lo + d): d = 1
-// is one live edge (probability 1); otherwise gap c takes the 64-bit uniform
-// of words 2(c&1), 2(c&1)+1 of the SKIP draw with counter words (v, c >> 1),
-// the next live edge is lo + pos + G, and the walk ends when G reaches past
-// the list.  Every round hands one live tail per lane to visit(u, lt_mask)
+// The gap walk of one weighted-cascade node as a state machine: one run, the
+// whole in-list, with t = wc_threshold(d) (d = 1: probability 1, every edge
+// live without a draw).  Gap c takes the 64-bit uniform of words 2(c&1),
+// 2(c&1)+1 of the SKIP draw with counter words (v, c >> 1); the next live
+// edge is rlo + pos + G, and the walk ends when G reaches past the list.
+struct GapWalk {
+  uint32_t lo = 0, d = 0;      // the node's in-list
+  uint32_t rlo = 0, rlen = 0;  // the run (absolute start, length)
+  uint32_t pos = 0, c = 0;     // position in the run; gaps drawn in it
+  uint32_t t = 0;              // the run's threshold
+  int k = -1, J = 0;           // run index; bit length of rlen
+  const uint64_t* P = nullptr;
+  uint64_t spare = 0;
+};
+
+// Move to the node's next nonempty run; false when none is left.
+__device__ __forceinline__ bool walk_next_run(GapWalk& w, const GraphView& g, uint64_t* own) {
+  ++w.k;
+  if (w.k > 0 || w.d == 0u) return false;
+  w.rlo = w.lo;
+  w.rlen = w.d;
+  w.J = 32 - __clz((int)w.d);
+  w.t = wc_threshold(w.d);
+  w.P = w.d >= 2u ? wc_power_row(g, w.d, w.J, own) : nullptr;
+  w.pos = 0;
+  w.c = 0;
+  return true;
+}
+
+// Start the walk of node v; false when it has no in-edges.
+__device__ __forceinline__ bool walk_begin(GapWalk& w, const GraphView& g, int32_t v, uint64_t* own) {
+  w.lo = (uint32_t)__ldg(g.off + v);
+  w.d = (uint32_t)__ldg(g.off + v + 1) - w.lo;
+  w.k = -1;
+  return walk_next_run(w, g, own);
+}
+
+// One step: the tail of the next live edge, or NO_NODE when the node has no
+// more; *more says whether the node may still give live edges.
+__device__ __forceinline__ uint32_t walk_step(GapWalk& w, const GraphView& g, int32_t v, const uint32_t* rk,
+                                              const SampleConst& skc, unsigned long long& draws, uint64_t* own,
+                                              bool* more) {
+  for (;;) {
+    uint32_t e;
+    if (w.t == 0xFFFFFFFFu) {
+      e = w.rlo + w.pos;
+      w.pos += 1u;
+    } else {
+      uint64_t U;
+      if (!(w.c & 1u)) {
+        const uint4 r = philox_xy((uint32_t)v, w.c >> 1, skc, rk);
+        ++draws;
+        U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+        w.spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
+      } else {
+        U = w.spare;
+      }
+      const uint32_t G = wc_gap(w.P, w.J, U);
+      if (G >= w.rlen - w.pos) {
+        if (walk_next_run(w, g, own)) continue;
+        *more = false;
+        return NO_NODE;
+      }
+      e = w.rlo + w.pos + G;
+      w.pos += G + 1u;
+      ++w.c;
+    }
+    *more = w.pos < w.rlen || walk_next_run(w, g, own);
+    return __ldg(&g.edge[e].x);
+  }
+}
+
+// Gap-walk IC expansion of up to 32 frontier nodes, one per lane (v = -1 for
+// none): every round hands one live tail per lane to visit(u, lt_mask)
 // (NO_NODE for idle lanes).  Returns visit's "stop".
 template <class Visit>
 __device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& skc,
                                           int lane, unsigned long long& ev, unsigned long long& draws,
                                           Visit&& visit) {
-  uint32_t lo = 0, d = 0;
+  uint64_t own[31];  // powers of a weighted-cascade in-degree beyond the graph's table
+  GapWalk w;
+  bool active = false;
   if (v >= 0) {
-    lo = (uint32_t)__ldg(g.off + v);
-    d = (uint32_t)__ldg(g.off + v + 1) - lo;
+    active = walk_begin(w, g, v, own);
+    ev += w.d;
   }
-  ev += d;
-  const int J = 32 - __clz((int)d);
-  uint64_t own[31];  // q^(2^i), i < J, when the graph's table has no row for d
-  const uint64_t* P = d >= 2u ? wc_power_row(g, d, J, own) : nullptr;
-  uint32_t pos = 0, c = 0;
-  uint64_t spare = 0;
-  bool active = d > 0u;
   const unsigned lt_mask = (1u << lane) - 1u;
   while (__any_sync(FULL_MASK, active)) {
     uint32_t u = NO_NODE;
-    if (active) {
-      uint32_t e = 0;
-      bool live = true;
-      if (d == 1u) {
-        e = lo;
-        active = false;
-      } else {
-        uint64_t U;
-        if (!(c & 1u)) {
-          const uint4 r = philox_xy((uint32_t)v, c >> 1, skc, rk);
-          ++draws;
-          U = (uint64_t)r.x | ((uint64_t)r.y << 32);
-          spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
-        } else {
-          U = spare;
-        }
-        const uint32_t G = wc_gap(P, J, U);
-        if (G >= d - pos) {
-          live = false;
-          active = false;
-        } else {
-          e = lo + pos + G;
-          pos += G + 1u;
-          ++c;
-          if (pos >= d) active = false;
-        }
-      }
-      if (live) u = __ldg(&g.edge[e].x);
-    }
+    if (active) u = walk_step(w, g, v, rk, skc, draws, own, &active);
     if (visit(u, lt_mask)) return true;
   }
   return false;
 }
 
-// Weighted-cascade BFS of one sample by one warp over its private queue
-// Q[0, tail) (head = 0 at the start): every lane holds at most one node and
-// takes one gap step per round; a lane whose node is done takes the next
-// queued node at the start of the next round, so the lanes stay busy while
-// the queue holds work (a node's walk is the gap walk of expand_wc, the same
-// keyed draws).  visit(u, lt_mask) appends new nodes to Q and advances tail
-// (which this function reads through the reference); it returns "stop".
+// Gap-walk BFS of one sample by one warp over its private queue Q[0, tail)
+// (head = 0 at the start): every lane holds at most one node and takes one
+// walk step per round; a lane whose node is done takes the next queued node
+// at the start of the next round, so the lanes stay busy while the queue holds
+// work.  visit(u, lt_mask) appends new nodes to Q and advances tail (which
+// this function reads through the reference); it returns "stop".
 template <class Visit>
 __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q, const int& tail,
                                             const uint32_t* rk, const SampleConst& skc, int lane,
@@ -376,11 +410,8 @@ __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q
   const unsigned lt_mask = (1u << lane) - 1u;
   int head = 0;
   int32_t v = -1;
-  uint32_t lo = 0, d = 0, pos = 0, c = 0;
-  int Jb = 0;
-  uint64_t spare = 0;
-  uint64_t own[31];  // q^(2^i), i < Jb, of the lane's node when the graph's table has no row for it
-  const uint64_t* P = nullptr;
+  GapWalk w;
+  uint64_t own[31];  // powers of a weighted-cascade in-degree beyond the graph's table
   for (;;) {
     __syncwarp();  // queue entries written by other lanes in the last round
     const bool need = v < 0;
@@ -390,44 +421,20 @@ __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q
       const int r = __popc(nm & lt_mask);
       if (r < take) {
         v = Q[head + r];
-        lo = (uint32_t)__ldg(g.off + v);
-        d = (uint32_t)__ldg(g.off + v + 1) - lo;
-        ev += d;
-        pos = 0;
-        c = 0;
-        Jb = 32 - __clz((int)d);
-        if (d >= 2u) P = wc_power_row(g, d, Jb, own);
+        if (!walk_begin(w, g, v, own)) v = -1;
+        ev += w.d;
       }
     }
     head += take;
-    if (!__any_sync(FULL_MASK, v >= 0)) break;  // queue drained, no lane holds a node
+    if (!__any_sync(FULL_MASK, v >= 0)) {
+      if (head >= tail) break;  // queue drained, no lane holds a node
+      continue;                 // every node taken this round had no in-edges
+    }
     uint32_t u = NO_NODE;
     if (v >= 0) {
-      if (d == 0u) {
-        v = -1;
-      } else if (d == 1u) {
-        u = __ldg(&g.edge[lo].x);
-        v = -1;
-      } else {
-        uint64_t U;
-        if (!(c & 1u)) {
-          const uint4 r = philox_xy((uint32_t)v, c >> 1, skc, rk);
-          ++draws;
-          U = (uint64_t)r.x | ((uint64_t)r.y << 32);
-          spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
-        } else {
-          U = spare;
-        }
-        const uint32_t G = wc_gap(P, Jb, U);
-        if (G >= d - pos) {
-          v = -1;
-        } else {
-          u = __ldg(&g.edge[lo + pos + G].x);
-          pos += G + 1u;
-          ++c;
-          if (pos >= d) v = -1;
-        }
-      }
+      bool more = true;
+      u = walk_step(w, g, v, rk, skc, draws, own, &more);
+      if (!more) v = -1;
     }
     if (visit(u, lt_mask)) return;
   }
@@ -705,36 +712,13 @@ __global__ void __launch_bounds__(256) k_sample_lane_wc(SampleJob J) {
     bool overflow = false;
     for (int h = 0; h < tail && !hit && !overflow; ++h) {
       const int32_t v = q[h];
-      const uint32_t lo = (uint32_t)__ldg(J.g.off + v);
-      const uint32_t d = (uint32_t)__ldg(J.g.off + v + 1) - lo;
-      ev += d;
-      if (d == 0u) continue;
-      const int Jb = 32 - __clz((int)d);
-      const uint64_t* P = d >= 2u ? wc_power_row(J.g, d, Jb, own) : nullptr;
-      uint32_t pos = 0, c = 0;
-      uint64_t spare = 0;
-      while (pos < d) {
-        uint32_t e;
-        if (d == 1u) {
-          e = lo;
-          pos = 1;
-        } else {
-          uint64_t U;
-          if (!(c & 1u)) {
-            const uint4 r = philox_xy((uint32_t)v, c >> 1, sc, J.rk);
-            ++dr;
-            U = (uint64_t)r.x | ((uint64_t)r.y << 32);
-            spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
-          } else {
-            U = spare;
-          }
-          const uint32_t G = wc_gap(P, Jb, U);
-          if (G >= d - pos) break;
-          e = lo + pos + G;
-          pos += G + 1u;
-          ++c;
-        }
-        const int32_t u = (int32_t)__ldg(&J.g.edge[e].x);
+      GapWalk w;
+      bool more = walk_begin(w, J.g, v, own);
+      ev += w.d;
+      while (more) {
+        const uint32_t u32 = walk_step(w, J.g, v, J.rk, sc, dr, own, &more);
+        if (u32 == NO_NODE) break;
+        const int32_t u = (int32_t)u32;
         bool seen = false;
         for (int i = 0; i < tail; ++i) seen |= q[i] == u;
         if (seen) continue;
@@ -943,13 +927,13 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
       };
       if constexpr (WC) {
         // Weighted cascade without level barriers: any visiting order reaches
-        // the same set (the gaps are keyed per node), so the warps pull up to
-        // 32 queued nodes at a time as they appear.  s_pending counts the
-        // nodes queued or being expanded: a warp adds the nodes it queues
-        // before it retires the chunk it expanded, so s_pending reaches 0 only
-        // when nothing is queued and no warp holds work, and the sample ends
-        // there.  A queue slot reads -1 until its node is written, so a claimed
-        // slot whose writer has reserved but not yet stored it is waited for.
+        // the same set (the gaps are keyed per node), so the warps pull queued
+        // nodes as they appear.  s_pending counts the nodes queued or being walked: a
+        // lane's new nodes are added before its node is retired, so s_pending
+        // reaches 0 only when nothing is queued and no lane holds a node, and
+        // the sample ends there.  A queue slot reads -1 until its node is
+        // written, so a claimed slot whose writer has reserved but not yet
+        // stored it is waited for.
         auto stopped = [&]() -> bool {
           return (MODE == MODE_HIT && *(volatile int*)&s_hit) || (KIND == 1 && *(volatile int*)&s_tail > qcap);
         };
@@ -960,45 +944,72 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
         __syncthreads();
         const int qlim = (int)(qcap < 0x7FFFFFFF ? qcap : 0x7FFFFFFF);  // queue slots that can be written
         long long idle = 0;
-        // Every claim and every decision is taken by lane 0 and broadcast, so
-        // the warp stays converged for the shuffles and ballots below.
+        // Every lane holds at most one node and takes one walk step per round;
+        // lanes without a node claim the next queued ones at the start of a
+        // round (one claim per warp, taken by lane 0 and broadcast, so the warp
+        // stays converged for the shuffles and ballots below).  A node is
+        // retired from s_pending when its walk is done, after the nodes it
+        // queued were added.
+        const unsigned lt_mask = (1u << lane) - 1u;
+        int32_t v = -1;
+        GapWalk w;
+        uint64_t own[31];  // powers of a weighted-cascade in-degree beyond the graph's table
         for (;;) {
           if (__any_sync(FULL_MASK, stopped())) break;
+          const bool need = v < 0;
+          const unsigned nm = __ballot_sync(FULL_MASK, need);
           int h = 0, cnt = 0;
-          if (lane == 0) {
+          if (lane == 0 && nm) {
+            const int want = __popc(nm);
             for (;;) {
               h = *(volatile int*)&s_head;
               const int avail = min(*(volatile int*)&s_tail, qlim) - h;
-              cnt = avail < 32 ? avail : 32;
+              cnt = avail < want ? avail : want;
               if (cnt <= 0 || atomicCAS(&s_head, h, h + cnt) == h) break;
             }
           }
           h = __shfl_sync(FULL_MASK, h, 0);
           cnt = __shfl_sync(FULL_MASK, cnt, 0);
-          if (cnt > 0) {
-            int32_t v = -1;
-            if (lane < cnt) {
+          bool empty = false;  // took a node that has no in-edges (or whose slot never arrived)
+          if (need) {
+            const int r = __popc(nm & lt_mask);
+            if (r < cnt) {
+              int32_t x;
               // the slot's writer has reserved it; wait (briefly) for its store
-              for (long long w = 0; (v = *(volatile int32_t*)&Q[h + lane]) < 0; ++w) {
-                if (w > (1ll << 22)) {
+              for (long long t = 0; (x = *(volatile int32_t*)&Q[h + r]) < 0; ++t) {
+                if (t > (1ll << 22)) {
                   atomicCAS(&J.ctr->error, 0u, SAMPLER_ERR_SLOT);
-                  v = -1;
+                  x = -1;
                   break;
                 }
               }
+              if (x >= 0 && walk_begin(w, J.g, x, own)) v = x;
+              else empty = true;
+              if (x >= 0) ev += w.d;
             }
-            expand_wc(J.g, v, J.rk, sc, lane, ev, dr, visit);
-            __syncwarp();
-            if (lane == 0) {
-              __threadfence_block();  // new queue entries before the chunk is retired
-              atomicSub(&s_pending, cnt);
+          }
+          uint32_t u = NO_NODE;
+          bool fin = false;
+          if (v >= 0) {
+            bool more = true;
+            u = walk_step(w, J.g, v, J.rk, sc, dr, own, &more);
+            if (!more) {
+              v = -1;
+              fin = true;
             }
+          }
+          if (visit(u, lt_mask)) break;
+          const int nret = __popc(__ballot_sync(FULL_MASK, fin || empty));
+          if (lane == 0 && nret) {
+            __threadfence_block();  // the nodes they queued before they are retired
+            atomicSub(&s_pending, nret);
+          }
+          if (cnt > 0 || nret > 0 || __any_sync(FULL_MASK, v >= 0)) {
             idle = 0;
             continue;
           }
-          // nothing to claim: the sample is done once nothing is pending
-          const int done = *(volatile int*)&s_pending == 0;
-          if (__any_sync(FULL_MASK, done)) break;
+          // nothing held and nothing to claim: the sample is done once nothing is pending
+          if (__any_sync(FULL_MASK, *(volatile int*)&s_pending == 0)) break;
           if (++idle > (1ll << 24)) {  // far longer than any sample: give up and report
             if (lane == 0) atomicCAS(&J.ctr->error, 0u, SAMPLER_ERR_IDLE);
             break;
