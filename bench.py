@@ -71,8 +71,8 @@ TRAFFIC = {
     # 2^23-node capture (profiles/sample_warp_wcg_wc_ic_rmat23.md): 14.14 GB of DRAM traffic over
     # 47,589,152 node visits for the lane and warp tiers of a 2M-set grow, scaled to the 2^25-node
     # workload by its node visits (the traffic is four to five random sector touches per visit)
-    ("ssa_ic_wc_rmat25_m1.3G_k100", "sample_warp"): {"src": "2668410468aba68a", "bytes_per_node_visit": 297.2},
-    ("ssa_ic_wc_rmat23_m128M_k100", "sample_warp"): {"src": "2668410468aba68a", "bytes_per_node_visit": 297.2},
+    ("ssa_ic_wc_rmat25_m1.3G_k100", "sample_warp"): {"src": "856e006a6deed4db", "bytes_per_node_visit": 297.2},
+    ("ssa_ic_wc_rmat23_m128M_k100", "sample_warp"): {"src": "856e006a6deed4db", "bytes_per_node_visit": 297.2},
 }
 
 

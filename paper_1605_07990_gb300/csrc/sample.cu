@@ -302,107 +302,69 @@ __device__ __forceinline__ uint32_t wc_gap(const uint64_t* P, int J, uint64_t U)
   return gap;
 }
 
-// The gap walk of one weighted-cascade node as a state machine: one run, the
-// whole in-list, with t = wc_threshold(d) (d = 1: probability 1, every edge
-// live without a draw).  Gap c takes the 64-bit uniform of words 2(c&1),
-// 2(c&1)+1 of the SKIP draw with counter words (v, c >> 1); the next live
-// edge is rlo + pos + G, and the walk ends when G reaches past the list.
+// The gap walk of one weighted-cascade node as a state machine, for the CTA
+// tier, whose lanes keep a node across rounds: d = 1 is one live edge
+// (probability 1, no draw); otherwise gap c takes the 64-bit uniform of
+// words 2(c&1), 2(c&1)+1 of the SKIP draw with counter words (v, c >> 1), the
+// next live edge is lo + pos + G, and the walk ends when G reaches past the
+// list.  (The lane tier and the warp BFS inline the same steps.)
 struct GapWalk {
-  uint32_t lo = 0, d = 0;      // the node's in-list
-  uint32_t rlo = 0, rlen = 0;  // the run (absolute start, length)
-  uint32_t pos = 0, c = 0;     // position in the run; gaps drawn in it
-  uint32_t t = 0;              // the run's threshold
-  int k = -1, J = 0;           // run index; bit length of rlen
+  uint32_t lo = 0, d = 0;   // the node's in-list
+  uint32_t pos = 0, c = 0;  // position in it; gaps drawn
+  int J = 0;                // bit length of d
   const uint64_t* P = nullptr;
   uint64_t spare = 0;
 };
-
-// Move to the node's next nonempty run; false when none is left.
-__device__ __forceinline__ bool walk_next_run(GapWalk& w, const GraphView& g, uint64_t* own) {
-  ++w.k;
-  if (w.k > 0 || w.d == 0u) return false;
-  w.rlo = w.lo;
-  w.rlen = w.d;
-  w.J = 32 - __clz((int)w.d);
-  w.t = wc_threshold(w.d);
-  w.P = w.d >= 2u ? wc_power_row(g, w.d, w.J, own) : nullptr;
-  w.pos = 0;
-  w.c = 0;
-  return true;
-}
 
 // Start the walk of node v; false when it has no in-edges.
 __device__ __forceinline__ bool walk_begin(GapWalk& w, const GraphView& g, int32_t v, uint64_t* own) {
   w.lo = (uint32_t)__ldg(g.off + v);
   w.d = (uint32_t)__ldg(g.off + v + 1) - w.lo;
-  w.k = -1;
-  return walk_next_run(w, g, own);
+  w.pos = 0;
+  w.c = 0;
+  w.J = 32 - __clz((int)w.d);
+  w.P = w.d >= 2u ? wc_power_row(g, w.d, w.J, own) : nullptr;
+  return w.d > 0u;
 }
 
 // One step: the tail of the next live edge, or NO_NODE when the node has no
 // more; *more says whether the node may still give live edges.
 __device__ __forceinline__ uint32_t walk_step(GapWalk& w, const GraphView& g, int32_t v, const uint32_t* rk,
-                                              const SampleConst& skc, unsigned long long& draws, uint64_t* own,
-                                              bool* more) {
-  for (;;) {
-    uint32_t e;
-    if (w.t == 0xFFFFFFFFu) {
-      e = w.rlo + w.pos;
-      w.pos += 1u;
+                                              const SampleConst& skc, unsigned long long& draws, bool* more) {
+  uint32_t e;
+  if (w.d == 1u) {
+    e = w.lo;
+    w.pos = 1;
+  } else {
+    uint64_t U;
+    if (!(w.c & 1u)) {
+      const uint4 r = philox_xy((uint32_t)v, w.c >> 1, skc, rk);
+      ++draws;
+      U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+      w.spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
     } else {
-      uint64_t U;
-      if (!(w.c & 1u)) {
-        const uint4 r = philox_xy((uint32_t)v, w.c >> 1, skc, rk);
-        ++draws;
-        U = (uint64_t)r.x | ((uint64_t)r.y << 32);
-        w.spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
-      } else {
-        U = w.spare;
-      }
-      const uint32_t G = wc_gap(w.P, w.J, U);
-      if (G >= w.rlen - w.pos) {
-        if (walk_next_run(w, g, own)) continue;
-        *more = false;
-        return NO_NODE;
-      }
-      e = w.rlo + w.pos + G;
-      w.pos += G + 1u;
-      ++w.c;
+      U = w.spare;
     }
-    *more = w.pos < w.rlen || walk_next_run(w, g, own);
-    return __ldg(&g.edge[e].x);
+    const uint32_t G = wc_gap(w.P, w.J, U);
+    if (G >= w.d - w.pos) {
+      *more = false;
+      return NO_NODE;
+    }
+    e = w.lo + w.pos + G;
+    w.pos += G + 1u;
+    ++w.c;
   }
+  *more = w.pos < w.d;
+  return __ldg(&g.edge[e].x);
 }
 
-// Gap-walk IC expansion of up to 32 frontier nodes, one per lane (v = -1 for
-// none): every round hands one live tail per lane to visit(u, lt_mask)
-// (NO_NODE for idle lanes).  Returns visit's "stop".
-template <class Visit>
-__device__ __forceinline__ bool expand_wc(const GraphView& g, int32_t v, const uint32_t* rk, const SampleConst& skc,
-                                          int lane, unsigned long long& ev, unsigned long long& draws,
-                                          Visit&& visit) {
-  uint64_t own[31];  // powers of a weighted-cascade in-degree beyond the graph's table
-  GapWalk w;
-  bool active = false;
-  if (v >= 0) {
-    active = walk_begin(w, g, v, own);
-    ev += w.d;
-  }
-  const unsigned lt_mask = (1u << lane) - 1u;
-  while (__any_sync(FULL_MASK, active)) {
-    uint32_t u = NO_NODE;
-    if (active) u = walk_step(w, g, v, rk, skc, draws, own, &active);
-    if (visit(u, lt_mask)) return true;
-  }
-  return false;
-}
-
-// Gap-walk BFS of one sample by one warp over its private queue Q[0, tail)
-// (head = 0 at the start): every lane holds at most one node and takes one
-// walk step per round; a lane whose node is done takes the next queued node
-// at the start of the next round, so the lanes stay busy while the queue holds
-// work.  visit(u, lt_mask) appends new nodes to Q and advances tail (which
-// this function reads through the reference); it returns "stop".
+// Weighted-cascade BFS of one sample by one warp over its private queue
+// Q[0, tail) (head = 0 at the start): every lane holds at most one node and
+// takes one gap step per round; a lane whose node is done takes the next
+// queued node at the start of the next round, so the lanes stay busy while
+// the queue holds work (a node's walk is the gap walk of walk_step, the same
+// keyed draws).  visit(u, lt_mask) appends new nodes to Q and advances tail
+// (which this function reads through the reference); it returns "stop".
 template <class Visit>
 __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q, const int& tail,
                                             const uint32_t* rk, const SampleConst& skc, int lane,
@@ -410,8 +372,11 @@ __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q
   const unsigned lt_mask = (1u << lane) - 1u;
   int head = 0;
   int32_t v = -1;
-  GapWalk w;
-  uint64_t own[31];  // powers of a weighted-cascade in-degree beyond the graph's table
+  uint32_t lo = 0, d = 0, pos = 0, c = 0;
+  int Jb = 0;
+  uint64_t spare = 0;
+  uint64_t own[31];  // q^(2^i), i < Jb, of the lane's node when the graph's table has no row for it
+  const uint64_t* P = nullptr;
   for (;;) {
     __syncwarp();  // queue entries written by other lanes in the last round
     const bool need = v < 0;
@@ -421,20 +386,44 @@ __device__ __forceinline__ void wc_bfs_warp(const GraphView& g, const int32_t* Q
       const int r = __popc(nm & lt_mask);
       if (r < take) {
         v = Q[head + r];
-        if (!walk_begin(w, g, v, own)) v = -1;
-        ev += w.d;
+        lo = (uint32_t)__ldg(g.off + v);
+        d = (uint32_t)__ldg(g.off + v + 1) - lo;
+        ev += d;
+        pos = 0;
+        c = 0;
+        Jb = 32 - __clz((int)d);
+        if (d >= 2u) P = wc_power_row(g, d, Jb, own);
       }
     }
     head += take;
-    if (!__any_sync(FULL_MASK, v >= 0)) {
-      if (head >= tail) break;  // queue drained, no lane holds a node
-      continue;                 // every node taken this round had no in-edges
-    }
+    if (!__any_sync(FULL_MASK, v >= 0)) break;  // queue drained, no lane holds a node
     uint32_t u = NO_NODE;
     if (v >= 0) {
-      bool more = true;
-      u = walk_step(w, g, v, rk, skc, draws, own, &more);
-      if (!more) v = -1;
+      if (d == 0u) {
+        v = -1;
+      } else if (d == 1u) {
+        u = __ldg(&g.edge[lo].x);
+        v = -1;
+      } else {
+        uint64_t U;
+        if (!(c & 1u)) {
+          const uint4 r = philox_xy((uint32_t)v, c >> 1, skc, rk);
+          ++draws;
+          U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+          spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
+        } else {
+          U = spare;
+        }
+        const uint32_t G = wc_gap(P, Jb, U);
+        if (G >= d - pos) {
+          v = -1;
+        } else {
+          u = __ldg(&g.edge[lo + pos + G].x);
+          pos += G + 1u;
+          ++c;
+          if (pos >= d) v = -1;
+        }
+      }
     }
     if (visit(u, lt_mask)) return;
   }
@@ -712,13 +701,36 @@ __global__ void __launch_bounds__(256) k_sample_lane_wc(SampleJob J) {
     bool overflow = false;
     for (int h = 0; h < tail && !hit && !overflow; ++h) {
       const int32_t v = q[h];
-      GapWalk w;
-      bool more = walk_begin(w, J.g, v, own);
-      ev += w.d;
-      while (more) {
-        const uint32_t u32 = walk_step(w, J.g, v, J.rk, sc, dr, own, &more);
-        if (u32 == NO_NODE) break;
-        const int32_t u = (int32_t)u32;
+      const uint32_t lo = (uint32_t)__ldg(J.g.off + v);
+      const uint32_t d = (uint32_t)__ldg(J.g.off + v + 1) - lo;
+      ev += d;
+      if (d == 0u) continue;
+      const int Jb = 32 - __clz((int)d);
+      const uint64_t* P = d >= 2u ? wc_power_row(J.g, d, Jb, own) : nullptr;
+      uint32_t pos = 0, c = 0;
+      uint64_t spare = 0;
+      while (pos < d) {
+        uint32_t e;
+        if (d == 1u) {
+          e = lo;
+          pos = 1;
+        } else {
+          uint64_t U;
+          if (!(c & 1u)) {
+            const uint4 r = philox_xy((uint32_t)v, c >> 1, sc, J.rk);
+            ++dr;
+            U = (uint64_t)r.x | ((uint64_t)r.y << 32);
+            spare = (uint64_t)r.z | ((uint64_t)r.w << 32);
+          } else {
+            U = spare;
+          }
+          const uint32_t G = wc_gap(P, Jb, U);
+          if (G >= d - pos) break;
+          e = lo + pos + G;
+          pos += G + 1u;
+          ++c;
+        }
+        const int32_t u = (int32_t)__ldg(&J.g.edge[e].x);
         bool seen = false;
         for (int i = 0; i < tail; ++i) seen |= q[i] == u;
         if (seen) continue;
@@ -992,7 +1004,7 @@ __global__ void __launch_bounds__(KIND == 1 ? SMALL_CTA_THREADS : 1024, KIND == 
           bool fin = false;
           if (v >= 0) {
             bool more = true;
-            u = walk_step(w, J.g, v, J.rk, sc, dr, own, &more);
+            u = walk_step(w, J.g, v, J.rk, sc, dr, &more);
             if (!more) {
               v = -1;
               fin = true;
