@@ -202,7 +202,10 @@ def roofline(kind, dom, ks, results, sm_count, clock_mhz, name, hbm_peak, hbm_ki
     traffic = None
     if tr and tr["src"] == kernel_source_hash():
         traffic = tr["bytes_per_node_visit"] * nv / launches
-    common = {"kernel": dom, "traffic": traffic, "avg_launch_ms": ks[dom]["ms"] / launches,
+    common = {"kernel": dom, "traffic": traffic,
+              # the DRAM rate the measured traffic implies over the class's CUDA-event time
+              "traffic_gbs": traffic / (ks[dom]["ms"] / launches / 1000.0) / 1e9 if traffic is not None else None,
+              "avg_launch_ms": ks[dom]["ms"] / launches,
               "node_visits_per_launch": nv / launches, "node_visits_per_s": nv / sec,
               "philox_draws_per_s": draws / sec}
     if kind == "ic_wc":

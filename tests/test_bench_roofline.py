@@ -52,6 +52,7 @@ def test_traffic_only_for_the_captured_source(monkeypatch):
     monkeypatch.setitem(bench.TRAFFIC, key, {"src": bench.kernel_source_hash(), "bytes_per_node_visit": 300.0})
     roof = bench.roofline("ic_wc", "sample_warp", ks, [r], 152, 2070.0, "w", 6789.6, "measured")
     assert roof["traffic"] == pytest.approx(300.0 * 1000 / 4)
+    assert roof["traffic_gbs"] == pytest.approx(300.0 * 1000 / 4 / (1.0 / 4 / 1000.0) / 1e9)
     monkeypatch.setitem(bench.TRAFFIC, key, {"src": "0000000000000000", "bytes_per_node_visit": 300.0})
     roof = bench.roofline("ic_wc", "sample_warp", ks, [r], 152, 2070.0, "w", 6789.6, "measured")
     assert roof["traffic"] is None
